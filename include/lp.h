@@ -1,0 +1,196 @@
+/*
+ * lp.h -- C ABI of the GB300 light-pollution convolution library (liblp.so).
+ *
+ * The library computes artificial night-sky-brightness maps as the linear
+ * two-dimensional convolution of a gridded ground-radiance map L1 with a
+ * shift-invariant point spread function K (Bara et al., arXiv:1907.02891):
+ *
+ *   B(r) = integral of K(r - r') L1(r') d^2 r'          Sec. 2.3, Eq. (7)
+ *
+ * discretised on the pixel grid (Eq. (2) with the factorable source of
+ * Eq. (3)) and evaluated through the convolution theorem, Sec. 2.3 Eq. (9):
+ * zero-pad both to a common size of at least N_L + N_K - 1 (Sec. 2.5), take
+ * the DFT of Eq. (10) by FFT, multiply pixel-wise, inverse FFT, crop.  The
+ * pixel-area factor of Eq. (2) is not applied; fold it into K.
+ *
+ * With 0-based indices, for a map L (h x w) and a PSF K (hk x wk, both odd,
+ * centre (cy, cx) = ((hk-1)/2, (wk-1)/2)):
+ *
+ *   Bfull[i][j] = sum_{i',j'} L[i'][j'] K[i-i'][j-j'],
+ *                 0 <= i < h+hk-1, 0 <= j < w+wk-1            (LP_OUT_FULL)
+ *   B[i][j]     = Bfull[i+cy][j+cx],  0 <= i < h, 0 <= j < w  (LP_OUT_SAME)
+ *
+ * LP_OUT_SAME puts every observer on a source pixel and keeps the map
+ * region; the sources all around it still contribute (Sec. 3).
+ *
+ * Conventions
+ *   - Pointers named "device" must be CUDA device pointers of the context's
+ *     device; "host" pointers are ordinary (preferably pinned) host memory.
+ *   - Matrices are row-major; ld* are leading dimensions in elements.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     All map calls are asynchronous on that stream.
+ *   - Every call returns lp_status.  Arguments are validated before anything
+ *     is launched; on error nothing is launched and lp_last_error() returns
+ *     a message (thread-local, valid until the next call on that thread).
+ *   - The caller owns L, K and out[]; the library owns plans, twiddle
+ *     tables, spectra, workspaces and its internal streams.  Inputs are
+ *     never written.  out[] must not overlap L.
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lp_status {
+    LP_OK = 0,
+    LP_ERR_INVALID = 1,     /* bad argument (null, size, leading dimension, padding) */
+    LP_ERR_OOM = 2,         /* device allocation failed or HBM budget exceeded */
+    LP_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    LP_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
+    LP_ERR_UNSUPPORTED = 5, /* size or precision not built into this library */
+    LP_ERR_BUSY = 6,        /* serving queue full / state does not allow the call */
+    LP_ERR_DEVICE = 7       /* a kernel reported an anomaly in the device status word */
+} lp_status;
+
+typedef enum lp_precision {
+    LP_PREC_FP32 = 0,       /* FP32 FFT path */
+    LP_PREC_SPLIT_BF16 = 1, /* reserved: split-BF16 tensor-core DFT stages */
+    LP_PREC_SPLIT_FP16 = 2  /* reserved: split-FP16 tensor-core DFT stages */
+} lp_precision;
+
+typedef enum lp_outmode {
+    LP_OUT_SAME = 0, /* h x w: the map region, observers on the source grid */
+    LP_OUT_FULL = 1  /* (h+hk-1) x (w+wk-1): the full linear convolution */
+} lp_outmode;
+
+typedef struct lp_ctx lp_ctx;
+typedef struct lp_spectrum lp_spectrum;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int lp_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lp_last_error(void);
+
+/*
+ * Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory the context holds (spectra + workspaces + staging); 0 means
+ * no cap.  Sets *ctx to NULL on failure.
+ */
+lp_status lp_create(lp_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Release everything the context owns (waits for its work to finish). */
+void lp_destroy(lp_ctx* ctx);
+
+/* Device bytes currently held by the context. */
+size_t lp_bytes_in_use(const lp_ctx* ctx);
+
+/*
+ * Supported padded FFT lengths (mixed radix, factors 2, 3, 5, 7).
+ * lp_supported_size(n) returns the smallest supported length >= n, or -1.
+ */
+int lp_num_supported_sizes(void);
+int lp_supported_size_at(int i);
+int lp_supported_size(int n);
+
+/*
+ * Kernel spectrum (Sec. 2.3 Eq. (9)-(10), padding of Sec. 2.5): the DFT of
+ * K zero-padded to pad_ny x pad_nx, computed in FP64 on the device and kept
+ * device-resident in FP32, scaled so that lp_map returns Eq. (7) directly.
+ *
+ *   K          device, FP64, hk x wk row-major (ld = wk); hk, wk odd; the
+ *              PSF centre is element ((hk-1)/2, (wk-1)/2).
+ *   max_h/w    largest map this spectrum will be used with; used only when
+ *              pad_ny / pad_nx is 0 (auto = smallest supported size
+ *              >= max_h + hk - 1, resp. max_w + wk - 1).
+ *   pad_ny/nx  explicit padded size (must be supported), or 0 for auto.
+ *   prec       LP_PREC_FP32 (others: LP_ERR_UNSUPPORTED in this build).
+ *   stream     the spectrum is ready in stream order; the call itself
+ *              synchronises the stream once (symmetry check).
+ *   out        receives a handle (refcounted: an identical request --
+ *              same values, sizes and precision -- returns the cached one).
+ *
+ * A point-symmetric K (K[cy+a][cx+b] == K[cy-a][cx-b] exactly) has a real
+ * spectrum and is stored as 4 bytes per bin, otherwise 8.
+ */
+lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, int wk, int max_h, int max_w,
+                             int pad_ny, int pad_nx, lp_precision prec, void* stream,
+                             lp_spectrum** out);
+
+/* Shape of a spectrum.  Any out pointer may be NULL. */
+lp_status lp_spectrum_info(const lp_spectrum* s, int* ny, int* nx, int* hk, int* wk,
+                           int* is_real);
+
+/*
+ * Copy the stored spectrum (device -> device) for inspection: layout
+ * (nx/2+1) rows x ny, row c holding the column-frequency c of every
+ * row-frequency u; FP32 real (is_real) or interleaved complex, scaled by
+ * 1/(2 ny nx).  dst_floats must be >= (nx/2+1)*ny*(is_real ? 1 : 2).
+ */
+lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t dst_floats, void* stream);
+
+/* Drop one reference; the spectrum is freed when the last one goes. */
+lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s);
+
+/*
+ * The map (steps S1-S6): B_k = K_k * L for each of the n spectra, from one
+ * shared forward transform of L (Sec. 3 computes several maps -- zenithal
+ * brightness and all-sky ratio -- from the same radiance map).
+ *
+ *   L        device FP32, h x w, leading dimension ldl >= w.
+ *   spectra  n >= 1 handles with identical (ny, nx), ny >= h + hk - 1 and
+ *            nx >= w + wk - 1 for each (the padding rule of Sec. 2.5); in
+ *            LP_OUT_FULL mode they must also share (hk, wk).
+ *   out      n device FP32 pointers, caller-allocated: h x w (SAME) or
+ *            (h+hk-1) x (w+wk-1) (FULL), leading dimension ldo.
+ *   prec     LP_PREC_FP32.
+ * Asynchronous on `stream`; use lp_sync_status to wait and collect device
+ * anomalies.  Calls on different streams of one context may overlap; each
+ * stream gets its own workspace.
+ */
+lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                 const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                 lp_outmode mode, lp_precision prec, void* stream);
+
+/*
+ * Same as lp_map with HOST buffers: copies L to the device, runs the map,
+ * copies every out[k] back, all in order on `stream` (the copies are
+ * asynchronous when the host memory is pinned).  Host buffers must stay
+ * valid until the stream reaches that point (lp_sync_status).
+ */
+lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w, int ldl,
+                      const lp_spectrum* const* spectra, int n, float* const* out_host, int ldo,
+                      lp_outmode mode, lp_precision prec, void* stream);
+
+/*
+ * Multi-class sources, Sec. 2.2 Eq. (4): B = sum_t K_t * L_t for T maps
+ * (device FP32, each h x w with leading dimension ldl) and T spectra (same
+ * rules as lp_map).  The spectrum products are summed before one inverse
+ * transform.  out: device FP32, leading dimension ldo.
+ */
+lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T, int h, int w, int ldl,
+                            const lp_spectrum* const* spectra, float* out, int ldo,
+                            lp_outmode mode, lp_precision prec, void* stream);
+
+/* Device bytes of workspace one lp_map call needs (0 if unsupported). */
+size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
+                              lp_outmode mode);
+
+/*
+ * Wait (bounded by timeout_ms; < 0 = no limit) for `stream`, then read and
+ * clear the context's sticky device status word.  LP_ERR_TIMEOUT if the
+ * stream is still busy, LP_ERR_DEVICE if a kernel flagged an anomaly,
+ * LP_ERR_CUDA for an asynchronous CUDA error.
+ */
+lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H */

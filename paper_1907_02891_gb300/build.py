@@ -1,0 +1,264 @@
+"""Build liblp.so (sm_103a) in-tree.
+
+The FP32 FFT kernels are templates over the radix sequence of each supported
+transform length.  This script picks one radix sequence per length (the
+plan table below), writes one small translation unit per length into
+``_build/gen``, and compiles everything with nvcc in parallel:
+
+    python -m paper_1907_02891_gb300.build          # or build() from Python
+
+Output: ``paper_1907_02891_gb300/_build/liblp.so``.
+"""
+
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+from typing import Dict, List, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+GEN = os.path.join(OUT, "gen")
+OBJ = os.path.join(OUT, "obj")
+LIB = os.path.join(OUT, "liblp.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+
+# radices the in-register DFTs are instantiated for (7-smooth, <= 32)
+RADICES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32)
+MAX_THREADS = 1024
+SMEM_LIMIT = 227 * 1024
+
+# Supported transform lengths.  Every length is 7-smooth; the list covers
+# the workload sizes (360, 480, 720, 1260, 2250, 4320, 4704, 8400, 8820,
+# 17280), powers of two, and a ladder in between.
+SIZES = (
+    45, 64, 96, 100, 120, 128, 160, 192, 210, 240, 256, 288, 320, 360, 384, 420, 480, 512,
+    560, 640, 720, 768, 840, 960, 1024, 1120, 1260, 1344, 1536, 1680, 1792, 2048, 2250, 2520,
+    2688, 3072, 3360, 3584, 4096, 4320, 4704, 5040, 5376, 6144, 6720, 7168, 8192, 8400, 8820,
+    10080, 10752, 12288, 13440, 15360, 16384, 17280,
+)
+
+
+def spad_size(n: int) -> int:
+    return n + (n >> 5) + 1
+
+
+def factorizations(n: int, max_stages: int = 4) -> List[Tuple[int, ...]]:
+    out: List[Tuple[int, ...]] = []
+
+    def rec(rem: int, start: int, cur: List[int]) -> None:
+        if rem == 1:
+            out.append(tuple(cur))
+            return
+        if len(cur) == max_stages:
+            return
+        for i in range(start, len(RADICES)):
+            r = RADICES[i]
+            if rem % r == 0:
+                rec(rem // r, i, cur + [r])
+
+    rec(n, 0, [])
+    return out
+
+
+def threads_for(n: int, radices: Sequence[int]) -> int:
+    return (n // min(radices) + 31) // 32 * 32
+
+
+def choose_plan(n: int) -> Tuple[int, ...]:
+    """Fewest stages; then the smallest largest radix (register pressure);
+    then the largest smallest radix (fewer threads).  Forward order is
+    descending, so the last forward radix -- whose outputs stay in registers
+    across the spectrum product -- is the smallest."""
+    best = None
+    for f in factorizations(n):
+        if threads_for(n, f) > MAX_THREADS:
+            continue
+        key = (len(f), max(f), -min(f))
+        if best is None or key < best[0]:
+            best = (key, f)
+    if best is None:
+        raise ValueError(f"no radix plan for {n}")
+    return tuple(sorted(best[1], reverse=True))
+
+
+def plan_table() -> Dict[int, dict]:
+    table = {}
+    for n in SIZES:
+        r = choose_plan(n)
+        t = threads_for(n, r)
+        smem = 2 * spad_size(n) * 4
+        if smem > SMEM_LIMIT:
+            raise ValueError(f"length {n} needs {smem} bytes of shared memory")
+
+        def fits(f: int) -> bool:
+            return f * t <= MAX_THREADS and f * smem <= 100 * 1024
+
+        # transforms per block in the row passes: two when they fit (32-byte
+        # column segments in T and U), one otherwise; more for tiny lengths
+        f = 1
+        for cand in (8, 4, 2):
+            if fits(cand) and (cand <= 2 or cand * t <= 256):
+                f = cand
+                break
+        table[n] = dict(radices=r, threads=t, f1=f, f3=f, smem=smem)
+    return table
+
+
+_SIZE_TU = """// generated by paper_1907_02891_gb300/build.py -- one supported FFT length
+#include "conv_kernels.cuh"
+#include "lp_internal.h"
+
+namespace lpk {{
+namespace {{
+constexpr int kN = {n};
+using P = Plan<kN, Seq<{seq}>>;
+constexpr int kF1 = {f1}, kF3 = {f3};
+constexpr int kSmem = P::SMEM_FLOATS * 4;
+
+template <class K>
+cudaError_t attr(K k, int bytes)
+{{
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}}
+
+cudaError_t set_attrs()
+{{
+    cudaError_t e;
+    if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_multiclass<P, kN, false>, kSmem)) != cudaSuccess) return e;
+    return attr(p3_rows<P, kN, kF3>, kF3 * kSmem);
+}}
+
+cudaError_t p1(const P1Args& a, int blocks, cudaStream_t s)
+{{
+    p1_rows<P, kN, kF1><<<blocks, P::T * kF1, kF1 * kSmem, s>>>(a);
+    return cudaGetLastError();
+}}
+
+cudaError_t p2(const P2Args& a, bool kreal, int blocks, cudaStream_t s)
+{{
+    if (kreal) p2_cols<P, kN, true><<<blocks, P::T, kSmem, s>>>(a);
+    else p2_cols<P, kN, false><<<blocks, P::T, kSmem, s>>>(a);
+    return cudaGetLastError();
+}}
+
+cudaError_t p2m(const P2MArgs& a, bool kreal, int blocks, cudaStream_t s)
+{{
+    if (kreal) p2_multiclass<P, kN, true><<<blocks, P::T, kSmem, s>>>(a);
+    else p2_multiclass<P, kN, false><<<blocks, P::T, kSmem, s>>>(a);
+    return cudaGetLastError();
+}}
+
+cudaError_t p3(const P3Args& a, int blocks, int nspec, cudaStream_t s)
+{{
+    p3_rows<P, kN, kF3><<<dim3(blocks, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
+    return cudaGetLastError();
+}}
+}}  // namespace
+
+extern const SizeKernels kSize_{n} = {{kN, {ns}, {{{rad6}}}, P::T, kF1, kF3, kSmem,
+                                       set_attrs, p1, p2, p2m, p3}};
+}}  // namespace lpk
+"""
+
+_REGISTRY_TU = """// generated by paper_1907_02891_gb300/build.py -- table of supported lengths
+#include "lp_internal.h"
+
+namespace lpk {{
+{decls}
+const SizeKernels* const kAllSizes[] = {{{ptrs}}};
+const int kNumSizes = {count};
+}}  // namespace lpk
+"""
+
+
+def _write_if_changed(path: str, text: str) -> None:
+    if os.path.exists(path):
+        with open(path) as fh:
+            if fh.read() == text:
+                return
+    with open(path, "w") as fh:
+        fh.write(text)
+
+
+def generate() -> List[str]:
+    os.makedirs(GEN, exist_ok=True)
+    table = plan_table()
+    files = []
+    for n, p in table.items():
+        r = list(p["radices"])
+        text = _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=p["f1"], f3=p["f3"], ns=len(r),
+                               rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
+        path = os.path.join(GEN, f"size_{n}.cu")
+        _write_if_changed(path, text)
+        files.append(path)
+    decls = "\n".join(f"extern const SizeKernels kSize_{n};" for n in table)
+    ptrs = ", ".join(f"&kSize_{n}" for n in table)
+    path = os.path.join(GEN, "registry.cu")
+    _write_if_changed(path, _REGISTRY_TU.format(decls=decls, ptrs=ptrs, count=len(table)))
+    files.append(path)
+    return files
+
+
+def _headers() -> List[str]:
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    hs.append(os.path.join(ROOT, "include", "lp.h"))
+    return hs
+
+
+def _compile(src: str, deps_mtime: float) -> str:
+    name = os.path.splitext(os.path.basename(src))[0]
+    digest = hashlib.sha1(src.encode()).hexdigest()[:8]
+    obj = os.path.join(OBJ, f"{name}_{digest}.o")
+    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), deps_mtime):
+        return obj
+    cmd = ["nvcc", *ARCH, *NVCC_FLAGS, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           "-c", src, "-o", obj + ".tmp"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(obj + ".tmp", obj)
+    return obj
+
+
+def build(jobs: int = 0, verbose: bool = False) -> str:
+    """Compile every CUDA/C++ source of the library for sm_103a and link
+    liblp.so.  Returns the library path."""
+    if shutil.which("nvcc") is None:
+        raise RuntimeError("nvcc not found on PATH")
+    os.makedirs(OBJ, exist_ok=True)
+    gen = generate()
+    srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cpp"))]
+    srcs += gen
+    deps = max(os.path.getmtime(h) for h in _headers() + [os.path.abspath(__file__)])
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        objs = list(ex.map(lambda s: _compile(s, deps), srcs))
+    if (not os.path.exists(LIB)) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
+    if verbose:
+        print(LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(verbose=True)
+    sys.exit(0)

@@ -1,0 +1,797 @@
+// C-ABI layer of liblp.so: argument validation, contexts, FFT plans and
+// twiddle tables, the device-resident PSF-spectrum cache, per-stream
+// workspaces and the launch sequence of the map (include/lp.h documents
+// every entry point).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lp.h"
+#include "conv_kernels.cuh"
+#include "lp_internal.h"
+#include "lp_runtime.h"
+
+using namespace lpk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+lp_status lp_fail(lp_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return lp_fail(e_ == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,     \
+                           "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                           __LINE__);                                                      \
+    } while (0)
+
+extern "C" const char* lp_last_error(void) { return g_err.c_str(); }
+extern "C" int lp_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+// supported sizes
+// ---------------------------------------------------------------------------
+static const SizeKernels* find_size(int n)
+{
+    for (int i = 0; i < kNumSizes; ++i)
+        if (kAllSizes[i]->N == n) return kAllSizes[i];
+    return nullptr;
+}
+
+extern "C" int lp_num_supported_sizes(void) { return kNumSizes; }
+extern "C" int lp_supported_size_at(int i) { return (i >= 0 && i < kNumSizes) ? kAllSizes[i]->N : -1; }
+extern "C" int lp_supported_size(int n)
+{
+    int best = -1;
+    for (int i = 0; i < kNumSizes; ++i) {
+        const int N = kAllSizes[i]->N;
+        if (N >= n && (best < 0 || N < best)) best = N;
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// device guard
+// ---------------------------------------------------------------------------
+namespace {
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context internals
+// ---------------------------------------------------------------------------
+lp_status lp_ctx_alloc(lp_ctx* ctx, size_t bytes, void** p)
+{
+    *p = nullptr;
+    if (bytes == 0) return LP_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        if (ctx->budget && ctx->used + bytes > ctx->budget)
+            return lp_fail(LP_ERR_OOM, "HBM budget: %zu bytes held + %zu requested > %zu", ctx->used,
+                           bytes, ctx->budget);
+        ctx->used += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        ctx->used -= bytes;
+        *p = nullptr;
+        return lp_fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+                       "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    return LP_OK;
+}
+
+void lp_ctx_free(lp_ctx* ctx, void* p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    ctx->used -= bytes;
+}
+
+// twiddle tables of one chain: stage s >= 1 holds (R_s - 1) * Ns entries
+static size_t chain_table_entries(const int* r, int ns)
+{
+    size_t tot = 0;
+    long Ns = r[0];
+    for (int s = 1; s < ns; ++s) {
+        tot += (size_t)(r[s] - 1) * Ns;
+        Ns *= r[s];
+    }
+    return tot;
+}
+
+static void fill_chain_tables(const int* r, int ns, std::vector<float2>& host, size_t base,
+                              size_t* offs)
+{
+    long Ns = r[0];
+    size_t o = base;
+    offs[0] = o;
+    for (int s = 1; s < ns; ++s) {
+        offs[s] = o;
+        const long n = Ns * r[s];
+        for (int m = 1; m < r[s]; ++m)
+            for (long k = 0; k < Ns; ++k) {
+                const long t = (k * m) % n;
+                const double th = 2.0 * M_PI * (double)t / (double)n;
+                host[o + (size_t)(m - 1) * Ns + k] = make_float2((float)std::cos(th), (float)-std::sin(th));
+            }
+        o += (size_t)(r[s] - 1) * Ns;
+        Ns *= r[s];
+    }
+}
+
+lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
+{
+    std::lock_guard<std::mutex> g(ctx->plan_mu);
+    auto it = ctx->plans.find(N);
+    if (it != ctx->plans.end()) {
+        *out = it->second.get();
+        return LP_OK;
+    }
+    const SizeKernels* k = find_size(N);
+    if (!k) return lp_fail(LP_ERR_UNSUPPORTED, "FFT length %d is not built into this library", N);
+    int fwd[6], rev[6];
+    const int ns = k->nstages;
+    for (int s = 0; s < ns; ++s) {
+        fwd[s] = k->radices[s];
+        rev[s] = k->radices[ns - 1 - s];
+    }
+    const size_t nf = chain_table_entries(fwd, ns), nr = chain_table_entries(rev, ns);
+    std::vector<float2> host(nf + nr + 1);
+    size_t of[6] = {0}, orv[6] = {0};
+    fill_chain_tables(fwd, ns, host, 0, of);
+    fill_chain_tables(rev, ns, host, nf, orv);
+    auto rec = std::make_unique<PlanRec>();
+    rec->k = k;
+    rec->bytes = host.size() * sizeof(float2);
+    void* d = nullptr;
+    lp_status st = lp_ctx_alloc(ctx, rec->bytes, &d);
+    if (st != LP_OK) return st;
+    rec->tw = static_cast<float2*>(d);
+    cudaError_t e = cudaMemcpy(rec->tw, host.data(), rec->bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        lp_ctx_free(ctx, d, rec->bytes);
+        return lp_fail(LP_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e));
+    }
+    for (int s = 0; s < 6; ++s) {
+        rec->fwd.p[s] = s < ns ? rec->tw + of[s] : nullptr;
+        rec->rev.p[s] = s < ns ? rec->tw + orv[s] : nullptr;
+    }
+    *out = rec.get();
+    ctx->plans.emplace(N, std::move(rec));
+    return LP_OK;
+}
+
+// per-stream workspace; grows (with a device sync) when a call needs more
+lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out)
+{
+    std::lock_guard<std::mutex> g(ctx->ws_mu);
+    Workspace* w = nullptr;
+    for (auto& x : ctx->ws)
+        if (x.stream == s) w = &x;
+    if (!w) {
+        ctx->ws.push_back(Workspace{s, nullptr, 0});
+        w = &ctx->ws.back();
+    }
+    if (w->bytes < bytes) {
+        if (w->ptr) {
+            cudaStreamSynchronize(s);
+            lp_ctx_free(ctx, w->ptr, w->bytes);
+            w->ptr = nullptr;
+            w->bytes = 0;
+        }
+        void* p = nullptr;
+        lp_status st = lp_ctx_alloc(ctx, bytes, &p);
+        if (st != LP_OK) return st;
+        w->ptr = p;
+        w->bytes = bytes;
+    }
+    *out = w->ptr;
+    return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// create / destroy
+// ---------------------------------------------------------------------------
+extern "C" lp_status lp_create(lp_ctx** ctx, int device, size_t hbm_budget_bytes)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_create: ctx is NULL");
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return lp_fail(LP_ERR_CUDA, "lp_create: no CUDA device available");
+    if (device < 0 || device >= ndev)
+        return lp_fail(LP_ERR_INVALID, "lp_create: device %d out of range [0,%d)", device, ndev);
+    DeviceGuard dg(device);
+    if (!dg.ok) return lp_fail(LP_ERR_CUDA, "lp_create: cudaSetDevice(%d) failed", device);
+    for (int i = 0; i < kNumSizes; ++i) CUDA_TRY(kAllSizes[i]->set_attrs());
+    auto c = new (std::nothrow) lp_ctx();
+    if (!c) return lp_fail(LP_ERR_OOM, "lp_create: host allocation failed");
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    void* e = nullptr;
+    lp_status st = lp_ctx_alloc(c, 64, &e);
+    if (st != LP_OK) {
+        delete c;
+        return st;
+    }
+    c->d_err = static_cast<int*>(e);
+    cudaMemset(c->d_err, 0, 64);
+    *ctx = c;
+    return LP_OK;
+}
+
+extern "C" void lp_destroy(lp_ctx* ctx)
+{
+    if (!ctx) return;
+    DeviceGuard dg(ctx->device);
+    lp_serve_shutdown(ctx);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->spectra) {
+        lp_ctx_free(ctx, kv.second->data, kv.second->bytes);
+        delete kv.second;
+    }
+    ctx->spectra.clear();
+    for (auto& w : ctx->ws) lp_ctx_free(ctx, w.ptr, w.bytes);
+    ctx->ws.clear();
+    for (auto& kv : ctx->plans) lp_ctx_free(ctx, kv.second->tw, kv.second->bytes);
+    ctx->plans.clear();
+    lp_ctx_free(ctx, ctx->staging, ctx->staging_bytes);
+    lp_ctx_free(ctx, ctx->d_err, 64);
+    delete ctx;
+}
+
+extern "C" size_t lp_bytes_in_use(const lp_ctx* ctx)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> g(const_cast<lp_ctx*>(ctx)->mem_mu);
+    return ctx->used;
+}
+
+// ---------------------------------------------------------------------------
+// spectra
+// ---------------------------------------------------------------------------
+extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, int wk, int max_h,
+                                        int max_w, int pad_ny, int pad_nx, lp_precision prec,
+                                        void* stream, lp_spectrum** out)
+{
+    if (out) *out = nullptr;
+    if (!ctx || !K || !out) return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: NULL argument");
+    if (hk < 1 || wk < 1 || hk % 2 == 0 || wk % 2 == 0)
+        return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: PSF sides must be odd and >= 1 (got %d x %d)", hk, wk);
+    if (prec != LP_PREC_FP32)
+        return lp_fail(LP_ERR_UNSUPPORTED, "lp_kernel_spectrum: precision %d is not built", (int)prec);
+    if (pad_ny < 0 || pad_nx < 0 || max_h < 0 || max_w < 0)
+        return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: negative size");
+    int Ny = pad_ny, Nx = pad_nx;
+    if (Ny == 0) {
+        if (max_h < 1) return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: need max_h or pad_ny");
+        Ny = lp_supported_size(max_h + hk - 1);
+        if (Ny < 0) return lp_fail(LP_ERR_UNSUPPORTED, "no supported FFT length >= %d", max_h + hk - 1);
+    }
+    if (Nx == 0) {
+        if (max_w < 1) return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: need max_w or pad_nx");
+        Nx = lp_supported_size(max_w + wk - 1);
+        if (Nx < 0) return lp_fail(LP_ERR_UNSUPPORTED, "no supported FFT length >= %d", max_w + wk - 1);
+    }
+    if (!find_size(Ny) || !find_size(Nx))
+        return lp_fail(LP_ERR_UNSUPPORTED, "padded size %d x %d is not a supported FFT length", Ny, Nx);
+    if (Ny < hk || Nx < wk)
+        return lp_fail(LP_ERR_INVALID, "padded size %d x %d is smaller than the PSF %d x %d", Ny, Nx, hk, wk);
+    if (!fft64_supported(Ny) || !fft64_supported(Nx))
+        return lp_fail(LP_ERR_UNSUPPORTED, "FP64 spectrum transform cannot factor %d x %d", Ny, Nx);
+
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, K) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
+        pa.device != ctx->device) {
+        cudaGetLastError();
+        return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: K is not a device pointer of device %d", ctx->device);
+    }
+    // plans used later by lp_map (allocating here keeps lp_map allocation-free
+    // once its workspace exists)
+    const PlanRec* pr;
+    lp_status s0 = lp_get_plan(ctx, Ny, &pr);
+    if (s0 != LP_OK) return s0;
+    s0 = lp_get_plan(ctx, Nx, &pr);
+    if (s0 != LP_OK) return s0;
+
+    // fingerprint + symmetry (one small device round trip)
+    unsigned long long* d_fp = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&d_fp, 16, st));
+    CUDA_TRY(cudaMemsetAsync(d_fp, 0, 16, st));
+    CUDA_TRY(psf_fingerprint_launch(K, (long long)hk * wk, d_fp, st));
+    CUDA_TRY(psf_symmetry_launch(K, hk, wk, reinterpret_cast<int*>(d_fp + 1), st));
+    unsigned long long host_fp[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(host_fp, d_fp, 16, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaFreeAsync(d_fp, st));
+    const int is_real = (int)(host_fp[1] & 0xffffffffull) == 0;
+    const SpecKey key{host_fp[0], hk, wk, Ny, Nx, (int)prec};
+    {
+        std::lock_guard<std::mutex> g(ctx->spec_mu);
+        auto it = ctx->spectra.find(key);
+        if (it != ctx->spectra.end()) {
+            it->second->refcount++;
+            *out = it->second;
+            return LP_OK;
+        }
+    }
+    const int ncols = Nx / 2 + 1;
+    const long long ldK = ((long long)Ny + 31) / 32 * 32;
+    const size_t bytes = (size_t)ncols * ldK * (is_real ? 4 : 8);
+    auto spec = new (std::nothrow) lp_spectrum();
+    if (!spec) return lp_fail(LP_ERR_OOM, "host allocation failed");
+    spec->ctx = ctx;
+    spec->key = key;
+    spec->ny = Ny;
+    spec->nx = Nx;
+    spec->hk = hk;
+    spec->wk = wk;
+    spec->is_real = is_real;
+    spec->prec = prec;
+    spec->ldK = ldK;
+    spec->bytes = bytes;
+    spec->refcount = 1;
+    void* dptr = nullptr;
+    lp_status sa = lp_ctx_alloc(ctx, bytes, &dptr);
+    if (sa != LP_OK) {
+        delete spec;
+        return sa;
+    }
+    spec->data = dptr;
+    // FP64 scratch, stream-ordered, released right after the build
+    const size_t w1 = sizeof(double2) * (size_t)hk * Nx;
+    const size_t w2 = sizeof(double2) * (size_t)Ny * ncols;
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&scratch, 2 * w1 + 2 * w2, st);
+    if (e != cudaSuccess) {
+        lp_ctx_free(ctx, dptr, bytes);
+        delete spec;
+        return lp_fail(LP_ERR_OOM, "spectrum scratch (%zu bytes): %s", 2 * w1 + 2 * w2, cudaGetErrorString(e));
+    }
+    cudaMemsetAsync(dptr, 0, bytes, st);
+    e = psf_spectrum_build(K, hk, wk, Ny, Nx, is_real, dptr, ldK, (double2*)scratch,
+                           (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
+                           (double2*)(scratch + 2 * w1 + w2), st);
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        lp_ctx_free(ctx, dptr, bytes);
+        delete spec;
+        return lp_fail(LP_ERR_CUDA, "spectrum build: %s", cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->spec_mu);
+        auto it = ctx->spectra.find(key);
+        if (it != ctx->spectra.end()) {  // another thread built the same one meanwhile
+            it->second->refcount++;
+            *out = it->second;
+            cudaStreamSynchronize(st);
+            lp_ctx_free(ctx, dptr, bytes);
+            delete spec;
+            return LP_OK;
+        }
+        ctx->spectra.emplace(key, spec);
+    }
+    *out = spec;
+    return LP_OK;
+}
+
+extern "C" lp_status lp_spectrum_info(const lp_spectrum* s, int* ny, int* nx, int* hk, int* wk,
+                                      int* is_real)
+{
+    if (!s) return lp_fail(LP_ERR_INVALID, "lp_spectrum_info: NULL spectrum");
+    if (ny) *ny = s->ny;
+    if (nx) *nx = s->nx;
+    if (hk) *hk = s->hk;
+    if (wk) *wk = s->wk;
+    if (is_real) *is_real = s->is_real;
+    return LP_OK;
+}
+
+extern "C" lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t dst_floats, void* stream)
+{
+    if (!s || !dst) return lp_fail(LP_ERR_INVALID, "lp_spectrum_copy: NULL argument");
+    const size_t per = s->is_real ? 1 : 2;
+    const size_t ncols = (size_t)s->nx / 2 + 1;
+    if (dst_floats < ncols * s->ny * per)
+        return lp_fail(LP_ERR_INVALID, "lp_spectrum_copy: destination holds %zu floats, need %zu",
+                       dst_floats, ncols * s->ny * per);
+    DeviceGuard dg(s->ctx->device);
+    CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)s->ny * per * 4, s->data, (size_t)s->ldK * per * 4,
+                               (size_t)s->ny * per * 4, ncols, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(stream)));
+    return LP_OK;
+}
+
+extern "C" lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s)
+{
+    if (!ctx || !s) return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: NULL argument");
+    if (s->ctx != ctx) return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: spectrum belongs to another context");
+    std::lock_guard<std::mutex> g(ctx->spec_mu);
+    auto it = ctx->spectra.find(s->key);
+    if (it == ctx->spectra.end() || it->second != s)
+        return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: unknown spectrum");
+    if (--s->refcount == 0) {
+        DeviceGuard dg(ctx->device);
+        cudaDeviceSynchronize();  // in-flight maps may still read it
+        lp_ctx_free(ctx, s->data, s->bytes);
+        ctx->spectra.erase(it);
+        delete s;
+    }
+    return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// map
+// ---------------------------------------------------------------------------
+static inline long long even_up(long long x) { return (x + 1) / 2 * 2; }
+
+// workspace layout: T (ncols x ldT) then U (n x ncols x ldU), complex64
+static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mode, MapDims* d)
+{
+    d->ncols = nx / 2 + 1;
+    d->ldT = even_up(h);
+    if (mode == LP_OUT_FULL) {
+        d->Hout = h + hk - 1;
+        d->Wout = w + wk - 1;
+        d->r0 = ny - (hk - 1) / 2;
+        d->c0 = nx - (wk - 1) / 2;
+        if (d->r0 == ny) d->r0 = 0;
+        if (d->c0 == nx) d->c0 = 0;
+    } else {
+        d->Hout = h;
+        d->Wout = w;
+        d->r0 = 0;
+        d->c0 = 0;
+    }
+    d->ldU = even_up(d->Hout);
+}
+
+extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
+                                         lp_outmode mode)
+{
+    if (h < 1 || w < 1 || ny < 1 || nx < 1 || n < 1 || hk < 1 || wk < 1) return 0;
+    MapDims d;
+    map_dims(h, w, ny, nx, hk, wk, mode, &d);
+    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
+    return 8ull * (size_t)d.ncols * (size_t)(d.ldT + (long long)nchunk * d.ldU) + 256;
+}
+
+lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                          const lp_spectrum* const* spectra, int n, const void* out, int ldo,
+                          lp_outmode mode, lp_precision prec, MapDims* d)
+{
+    if (!ctx || !L || !spectra || !out) return lp_fail(LP_ERR_INVALID, "lp_map: NULL argument");
+    if (h < 1 || w < 1) return lp_fail(LP_ERR_INVALID, "lp_map: empty map %d x %d", h, w);
+    if (ldl < w) return lp_fail(LP_ERR_INVALID, "lp_map: ldl %d < w %d", ldl, w);
+    if (n < 1) return lp_fail(LP_ERR_INVALID, "lp_map: need at least one spectrum");
+    if (mode != LP_OUT_SAME && mode != LP_OUT_FULL) return lp_fail(LP_ERR_INVALID, "lp_map: bad output mode");
+    if (prec != LP_PREC_FP32) return lp_fail(LP_ERR_UNSUPPORTED, "lp_map: precision %d is not built", (int)prec);
+    const lp_spectrum* s0 = spectra[0];
+    if (!s0) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum 0 is NULL");
+    for (int k = 0; k < n; ++k) {
+        const lp_spectrum* s = spectra[k];
+        if (!s) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum %d is NULL", k);
+        if (s->ctx != ctx) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum %d belongs to another context", k);
+        if (s->ny != s0->ny || s->nx != s0->nx)
+            return lp_fail(LP_ERR_INVALID, "lp_map: spectra differ in padded size (%dx%d vs %dx%d)", s->ny,
+                           s->nx, s0->ny, s0->nx);
+        if (s->ny < h + s->hk - 1 || s->nx < w + s->wk - 1)
+            return lp_fail(LP_ERR_INVALID,
+                           "lp_map: spectrum %d padded to %d x %d, the map %d x %d with a %d x %d PSF "
+                           "needs >= %d x %d",
+                           k, s->ny, s->nx, h, w, s->hk, s->wk, h + s->hk - 1, w + s->wk - 1);
+        if (mode == LP_OUT_FULL && (s->hk != s0->hk || s->wk != s0->wk))
+            return lp_fail(LP_ERR_INVALID, "lp_map: FULL output needs spectra of equal PSF size");
+        if (s->prec != prec) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum %d has another precision", k);
+    }
+    map_dims(h, w, s0->ny, s0->nx, s0->hk, s0->wk, mode, d);
+    if (ldo < d->Wout) return lp_fail(LP_ERR_INVALID, "lp_map: ldo %d < output width %d", ldo, d->Wout);
+    return LP_OK;
+}
+
+// Launch P1, P2, P3 for n spectra (the validated sequence of lp_map).
+lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                        const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                        const MapDims& d, void* ws, cudaStream_t st)
+{
+    const lp_spectrum* s0 = spectra[0];
+    const PlanRec *py, *px;
+    lp_status ps = lp_get_plan(ctx, s0->ny, &py);
+    if (ps != LP_OK) return ps;
+    ps = lp_get_plan(ctx, s0->nx, &px);
+    if (ps != LP_OK) return ps;
+    float2* T = static_cast<float2*>(ws);
+    float2* U = T + (size_t)d.ncols * d.ldT;
+    const int npairs = (int)(d.ldT / 2);
+
+    P1Args a1;
+    a1.L = L;
+    a1.ldl = ldl;
+    a1.H = h;
+    a1.W = w;
+    a1.T = T;
+    a1.ldT = d.ldT;
+    a1.npairs = npairs;
+    a1.ncols = d.ncols;
+    a1.tw = px->fwd;
+    const int f1 = px->k->f1;
+    CUDA_TRY(px->k->p1(a1, (npairs + f1 - 1) / f1, st));
+
+    for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
+        const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
+        // the real-spectrum kernel needs every spectrum of the launch real;
+        // split the chunk by kind
+        int k0 = 0;
+        while (k0 < cnt) {
+            const int kind = spectra[base + k0]->is_real;
+            int k1 = k0;
+            while (k1 < cnt && spectra[base + k1]->is_real == kind) ++k1;
+            P2Args a2;
+            a2.T = T;
+            a2.ldT = d.ldT;
+            a2.H = h;
+            for (int i = 0; i < kMaxSpectraPerLaunch; ++i)
+                a2.K[i] = (i < k1 - k0) ? spectra[base + k0 + i]->data : nullptr;
+            a2.ldK = s0->ldK;
+            a2.nspec = k1 - k0;
+            a2.U = U + (size_t)k0 * d.ncols * d.ldU;
+            a2.ldU = d.ldU;
+            a2.specU = (long long)d.ncols * d.ldU;
+            a2.r0 = d.r0;
+            a2.Hout = d.Hout;
+            a2.HoutPad = (int)d.ldU;
+            a2.ncols = d.ncols;
+            a2.twf = py->fwd;
+            a2.twi = py->rev;
+            CUDA_TRY(py->k->p2(a2, kind != 0, d.ncols, st));
+            k0 = k1;
+        }
+        P3Args a3;
+        a3.U = U;
+        a3.ldU = d.ldU;
+        a3.specU = (long long)d.ncols * d.ldU;
+        a3.Hout = d.Hout;
+        a3.npairs = (int)(d.ldU / 2);
+        for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i < cnt ? out[base + i] : nullptr;
+        a3.ldo = ldo;
+        a3.c0 = d.c0;
+        a3.Wout = d.Wout;
+        a3.ncols = d.ncols;
+        a3.tw = px->rev;
+        const int f3 = px->k->f3;
+        CUDA_TRY(px->k->p3(a3, (a3.npairs + f3 - 1) / f3, cnt, st));
+    }
+    return LP_OK;
+}
+
+extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                            const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                            lp_outmode mode, lp_precision prec, void* stream)
+{
+    MapDims d;
+    lp_status st = lp_validate_map(ctx, L, h, w, ldl, spectra, n, out, ldo, mode, prec, &d);
+    if (st != LP_OK) return st;
+    for (int k = 0; k < n; ++k) {
+        if (!out[k]) return lp_fail(LP_ERR_INVALID, "lp_map: out[%d] is NULL", k);
+        const char* o0 = reinterpret_cast<const char*>(out[k]);
+        const char* o1 = o0 + 4ull * ((size_t)(d.Hout - 1) * ldo + d.Wout);
+        const char* l0 = reinterpret_cast<const char*>(L);
+        const char* l1 = l0 + 4ull * ((size_t)(h - 1) * ldl + w);
+        if (o0 < l1 && l0 < o1) return lp_fail(LP_ERR_INVALID, "lp_map: out[%d] overlaps L", k);
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const lp_spectrum* s0 = spectra[0];
+    void* ws = nullptr;
+    st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
+    if (st != LP_OK) return st;
+    return lp_launch_map(ctx, L, h, w, ldl, spectra, n, out, ldo, d, ws, s);
+}
+
+extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w, int ldl,
+                                 const lp_spectrum* const* spectra, int n, float* const* out_host,
+                                 int ldo, lp_outmode mode, lp_precision prec, void* stream)
+{
+    MapDims d;
+    lp_status st = lp_validate_map(ctx, L_host, h, w, ldl, spectra, n, out_host, ldo, mode, prec, &d);
+    if (st != LP_OK) return st;
+    for (int k = 0; k < n; ++k)
+        if (!out_host[k]) return lp_fail(LP_ERR_INVALID, "lp_map_host: out[%d] is NULL", k);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const lp_spectrum* s0 = spectra[0];
+    // staging: L (h x w, packed) then n outputs (Hout x Wout, packed)
+    const size_t lbytes = 4ull * (size_t)h * w;
+    const size_t obytes = 4ull * (size_t)d.Hout * d.Wout;
+    const size_t need = ((lbytes + 255) / 256 * 256) + (size_t)n * ((obytes + 255) / 256 * 256);
+    {
+        std::lock_guard<std::mutex> g(ctx->ws_mu);
+        if (ctx->staging_bytes < need) {
+            if (ctx->staging) {
+                cudaDeviceSynchronize();
+                lp_ctx_free(ctx, ctx->staging, ctx->staging_bytes);
+                ctx->staging = nullptr;
+                ctx->staging_bytes = 0;
+            }
+            void* p = nullptr;
+            st = lp_ctx_alloc(ctx, need, &p);
+            if (st != LP_OK) return st;
+            ctx->staging = p;
+            ctx->staging_bytes = need;
+        }
+    }
+    char* base = static_cast<char*>(ctx->staging);
+    float* dL = reinterpret_cast<float*>(base);
+    std::vector<float*> dout(n);
+    char* p = base + (lbytes + 255) / 256 * 256;
+    for (int k = 0; k < n; ++k) {
+        dout[k] = reinterpret_cast<float*>(p);
+        p += (obytes + 255) / 256 * 256;
+    }
+    CUDA_TRY(cudaMemcpy2DAsync(dL, 4ull * w, L_host, 4ull * ldl, 4ull * w, h, cudaMemcpyHostToDevice, s));
+    void* ws = nullptr;
+    st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
+    if (st != LP_OK) return st;
+    st = lp_launch_map(ctx, dL, h, w, w, spectra, n, dout.data(), d.Wout, d, ws, s);
+    if (st != LP_OK) return st;
+    for (int k = 0; k < n; ++k)
+        CUDA_TRY(cudaMemcpy2DAsync(out_host[k], 4ull * ldo, dout[k], 4ull * d.Wout, 4ull * d.Wout, d.Hout,
+                                   cudaMemcpyDeviceToHost, s));
+    return LP_OK;
+}
+
+extern "C" lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_sync_status: NULL context");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(s);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady)
+            return lp_fail(LP_ERR_CUDA, "lp_sync_status: %s", cudaGetErrorString(q));
+        if (timeout_ms >= 0) {
+            const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ms) return lp_fail(LP_ERR_TIMEOUT, "lp_sync_status: stream busy after %d ms", timeout_ms);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    int herr = 0;
+    CUDA_TRY(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) {
+        CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return lp_fail(LP_ERR_DEVICE, "lp_sync_status: device status word 0x%x", herr);
+    }
+    return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (4): several source classes
+// ---------------------------------------------------------------------------
+extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T, int h, int w,
+                                       int ldl, const lp_spectrum* const* spectra, float* out,
+                                       int ldo, lp_outmode mode, lp_precision prec, void* stream)
+{
+    if (!L || T < 1) return lp_fail(LP_ERR_INVALID, "lp_map_multiclass: need T >= 1 maps");
+    if (T > kMaxSpectraPerLaunch)
+        return lp_fail(LP_ERR_INVALID, "lp_map_multiclass: at most %d classes", kMaxSpectraPerLaunch);
+    for (int t = 0; t < T; ++t)
+        if (!L[t]) return lp_fail(LP_ERR_INVALID, "lp_map_multiclass: L[%d] is NULL", t);
+    MapDims d;
+    lp_status st = lp_validate_map(ctx, L[0], h, w, ldl, spectra, T, out, ldo, mode, prec, &d);
+    if (st != LP_OK) return st;
+    if (mode == LP_OUT_SAME) {
+        // the crop offset is zero for every spectrum; FULL needs equal PSF sizes (checked)
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const lp_spectrum* s0 = spectra[0];
+    const PlanRec *py, *px;
+    if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
+    if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
+    const size_t tbytes = 8ull * (size_t)d.ncols * d.ldT;
+    const size_t ubytes = 8ull * (size_t)d.ncols * d.ldU;
+    void* ws = nullptr;
+    if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + 256, &ws)) != LP_OK) return st;
+    float2* Tb = static_cast<float2*>(ws);
+    float2* U = Tb + (size_t)T * d.ncols * d.ldT;
+    const int npairs = (int)(d.ldT / 2);
+    for (int t = 0; t < T; ++t) {
+        P1Args a1;
+        a1.L = L[t];
+        a1.ldl = ldl;
+        a1.H = h;
+        a1.W = w;
+        a1.T = Tb + (size_t)t * d.ncols * d.ldT;
+        a1.ldT = d.ldT;
+        a1.npairs = npairs;
+        a1.ncols = d.ncols;
+        a1.tw = px->fwd;
+        CUDA_TRY(px->k->p1(a1, (npairs + px->k->f1 - 1) / px->k->f1, s));
+    }
+    // the real-spectrum kernel needs every class's spectrum real
+    bool all_real = true;
+    for (int t = 0; t < T; ++t) all_real = all_real && spectra[t]->is_real;
+    if (!all_real)
+        for (int t = 0; t < T; ++t)
+            if (spectra[t]->is_real)
+                return lp_fail(LP_ERR_UNSUPPORTED,
+                               "lp_map_multiclass: mixing real and complex spectra is not supported");
+    P2MArgs a2;
+    for (int i = 0; i < kMaxSpectraPerLaunch; ++i) {
+        a2.T[i] = i < T ? Tb + (size_t)i * d.ncols * d.ldT : nullptr;
+        a2.K[i] = i < T ? spectra[i]->data : nullptr;
+    }
+    a2.ldT = d.ldT;
+    a2.H = h;
+    a2.ldK = s0->ldK;
+    a2.nclass = T;
+    a2.U = U;
+    a2.ldU = d.ldU;
+    a2.r0 = d.r0;
+    a2.Hout = d.Hout;
+    a2.HoutPad = (int)d.ldU;
+    a2.ncols = d.ncols;
+    a2.twf = py->fwd;
+    a2.twi = py->rev;
+    CUDA_TRY(py->k->p2m(a2, all_real, d.ncols, s));
+    P3Args a3;
+    a3.U = U;
+    a3.ldU = d.ldU;
+    a3.specU = 0;
+    a3.Hout = d.Hout;
+    a3.npairs = (int)(d.ldU / 2);
+    for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i == 0 ? out : nullptr;
+    a3.ldo = ldo;
+    a3.c0 = d.c0;
+    a3.Wout = d.Wout;
+    a3.ncols = d.ncols;
+    a3.tw = px->rev;
+    CUDA_TRY(px->k->p3(a3, (a3.npairs + px->k->f3 - 1) / px->k->f3, 1, s));
+    return LP_OK;
+}

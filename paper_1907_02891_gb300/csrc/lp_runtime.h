@@ -1,0 +1,81 @@
+// Host-side state of a context (shared by api.cu and serve.cpp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lp.h"
+#include "lp_internal.h"
+
+struct SpecKey {
+    unsigned long long fp;  // order-independent fingerprint of the PSF values
+    int hk, wk, ny, nx, prec;
+    bool operator<(const SpecKey& o) const
+    {
+        return std::tie(fp, hk, wk, ny, nx, prec) < std::tie(o.fp, o.hk, o.wk, o.ny, o.nx, o.prec);
+    }
+};
+
+struct PlanRec {
+    const lpk::SizeKernels* k = nullptr;
+    float2* tw = nullptr;  // device twiddle tables (forward chain, then reversed chain)
+    size_t bytes = 0;
+    lpk::TwChain fwd{}, rev{};
+};
+
+struct Workspace {
+    cudaStream_t stream;
+    void* ptr;
+    size_t bytes;
+};
+
+struct MapDims {
+    int ncols;          // Nx/2 + 1
+    long long ldT, ldU; // leading dimensions of T and U (complex elements, even)
+    int Hout, Wout;     // output size
+    int r0, c0;         // first kept row / column of the circular result
+};
+
+struct ServeState;
+
+struct lp_spectrum {
+    lp_ctx* ctx = nullptr;
+    SpecKey key{};
+    int ny = 0, nx = 0, hk = 0, wk = 0, is_real = 0;
+    lp_precision prec = LP_PREC_FP32;
+    long long ldK = 0;  // elements per stored column-frequency row
+    size_t bytes = 0;
+    int refcount = 0;
+    void* data = nullptr;
+};
+
+struct lp_ctx {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    std::mutex mem_mu, plan_mu, spec_mu, ws_mu;
+    std::map<int, std::unique_ptr<PlanRec>> plans;
+    std::map<SpecKey, lp_spectrum*> spectra;
+    std::vector<Workspace> ws;
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    int* d_err = nullptr;  // sticky device status word
+    ServeState* serve = nullptr;
+};
+
+lp_status lp_fail(lp_status st, const char* fmt, ...);
+lp_status lp_ctx_alloc(lp_ctx* ctx, size_t bytes, void** p);
+void lp_ctx_free(lp_ctx* ctx, void* p, size_t bytes);
+lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out);
+lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out);
+lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                          const lp_spectrum* const* spectra, int n, const void* out, int ldo,
+                          lp_outmode mode, lp_precision prec, MapDims* d);
+lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                        const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                        const MapDims& d, void* ws, cudaStream_t st);
+void lp_serve_shutdown(lp_ctx* ctx);

@@ -1,0 +1,308 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Error metric: max |B - B_ref| / max |B_ref| over the evaluated pixels; the
+bar for the FP32 path is 1e-5.  Full maps for small cases; on the full-size
+workloads, 4096 seeded pixels plus the 64 brightest pixels of the GPU
+output (so that the denominator is the global maximum).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_02891_gb300 import lp  # noqa: E402
+
+TOL_FP32 = 1e-5
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lp.lp_create(0)
+    yield c
+    lp.lp_destroy(c)
+
+
+def err_maxnorm(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run_map(ctx, L, Ks, mode=lp.LP_OUT_SAME, pad=None):
+    h, w = L.shape
+    specs = []
+    for K in Ks:
+        if pad is None:
+            specs.append(lp.lp_kernel_spectrum(ctx, dev(K), max_h=h, max_w=w))
+        else:
+            specs.append(lp.lp_kernel_spectrum(ctx, dev(K), pad_ny=pad[0], pad_nx=pad[1]))
+    hk, wk = Ks[0].shape
+    shape = lp.output_shape(h, w, hk, wk, mode)
+    outs = [torch.empty(shape, dtype=torch.float32, device=DEV) for _ in Ks]
+    lp.lp_map(ctx, dev(L), specs, outs, mode=mode)
+    lp.lp_sync_status(ctx)
+    res = [o.cpu().numpy() for o in outs]
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+    return res
+
+
+def wrap_place(K, ny, nx):
+    hk, wk = K.shape
+    cy, cx = (hk - 1) // 2, (wk - 1) // 2
+    Kw = np.zeros((ny, nx))
+    for y in range(hk):
+        for x in range(wk):
+            Kw[(y - cy) % ny, (x - cx) % nx] = K[y, x]
+    return Kw
+
+
+# --- S0: the spectrum is Eq. (10) of the wrap-placed PSF -------------------
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_spectrum_is_eq10_dft(ctx, symmetric):
+    g = np.random.default_rng(11)
+    ny, nx = 45, 64
+    if symmetric:
+        K = synth.psf_power_exp(7, 1.0, 0.25, 1.25, 40.0)[:, 1:6]   # 7 x 5, point-symmetric
+    else:
+        K = g.uniform(0.1, 1.0, (5, 7))
+    s = lp.lp_kernel_spectrum(ctx, dev(K), pad_ny=ny, pad_nx=nx)
+    info = lp.lp_spectrum_info(s)
+    assert (info["ny"], info["nx"], info["hk"], info["wk"]) == (ny, nx) + K.shape
+    assert info["is_real"] == symmetric
+    nc = nx // 2 + 1
+    per = 1 if symmetric else 2
+    buf = torch.empty(nc * ny * per, dtype=torch.float32, device=DEV)
+    lp.lp_spectrum_copy(s, buf)
+    torch.cuda.synchronize()
+    got = buf.cpu().numpy().astype(np.float64)
+    got = got.reshape(nc, ny) if symmetric else (got[0::2] + 1j * got[1::2]).reshape(nc, ny)
+    uu, cc = np.meshgrid(np.arange(ny), np.arange(nc), indexing="ij")
+    ref = oracle.dft2_points(wrap_place(K, ny, nx), uu, cc).reshape(ny, nc).T / (2.0 * ny * nx)
+    scale = np.max(np.abs(ref))
+    if symmetric:
+        assert np.max(np.abs(ref.imag)) < 1e-12 * scale
+        ref = ref.real
+    assert np.max(np.abs(got - ref)) < 2e-7 * scale
+    lp.lp_spectrum_release(ctx, s)
+
+
+# --- the whole path, small and full ------------------------------------------
+
+def test_map256_psf101_full_map(ctx):
+    wl = synth.WORKLOADS["map256_psf101"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_map(ctx, L, [K])
+    assert err_maxnorm(B, oracle.conv_same(L, K)) <= TOL_FP32
+    (Bf,) = run_map(ctx, L, [K], mode=lp.LP_OUT_FULL)
+    assert Bf.shape == (356, 356)
+    assert err_maxnorm(Bf, oracle.conv_full(L, K)) <= TOL_FP32
+
+
+def _pairs():
+    sizes = lp.supported_sizes()
+    n = len(sizes)
+    return [(sizes[i], sizes[(i * 7 + 3) % n]) for i in range(n)]
+
+
+@pytest.mark.parametrize("ny,nx", _pairs())
+def test_every_fft_length(ctx, ny, nx):
+    """Each supported length once as the column length (P2) and once as the
+    row length (P1, P3); a ragged map inside the padded grid."""
+    g = np.random.default_rng(ny * 100003 + nx)
+    hk = 9 if min(ny, nx) >= 40 else 5
+    wk = 7 if min(ny, nx) >= 40 else 3
+    h = min(ny - hk + 1, 93)
+    w = min(nx - wk + 1, 71)
+    L = g.lognormal(0.0, 1.0, (h, w)).astype(np.float32)
+    K = g.uniform(0.05, 1.0, (hk, wk))              # asymmetric: complex spectrum
+    Ksym = synth.psf_power_exp(hk, 1.0, 0.25, 1.25, 40.0)[:, (hk - wk) // 2:(hk + wk) // 2]
+    mode = lp.LP_OUT_FULL if (ny + nx) % 2 else lp.LP_OUT_SAME
+    B, Bs = run_map(ctx, L, [K, Ksym], mode=mode, pad=(ny, nx))
+    conv = oracle.conv_full if mode == lp.LP_OUT_FULL else oracle.conv_same
+    assert err_maxnorm(B, conv(L, K)) <= TOL_FP32
+    assert err_maxnorm(Bs, conv(L, Ksym)) <= TOL_FP32
+
+
+def test_ragged_leading_dimensions_and_mixed_spectra(ctx):
+    g = np.random.default_rng(12)
+    big = g.lognormal(0.0, 1.0, (41, 64)).astype(np.float32)
+    L = big[2:39, 5:58]                                   # 37 x 53, ldl = 64
+    Ks = [g.uniform(0.1, 1.0, (9, 11)), synth.psf_power_exp(11, 1.0, 0.1, 1.25, 80.0),
+          g.uniform(0.1, 1.0, (9, 11))]
+    Ks[1] = Ks[1][1:10, :]
+    Ld = dev(big)[2:39, 5:58]
+    for mode in (lp.LP_OUT_SAME, lp.LP_OUT_FULL):
+        specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=37, max_w=53) for K in Ks]
+        shape = lp.output_shape(37, 53, 9, 11, mode)
+        store = torch.full((3, shape[0], shape[1] + 6), float("nan"), device=DEV)
+        outs = [store[k, :, :shape[1]] for k in range(3)]
+        lp.lp_map(ctx, Ld, specs, outs, mode=mode)
+        lp.lp_sync_status(ctx)
+        conv = oracle.conv_full if mode == lp.LP_OUT_FULL else oracle.conv_same
+        for k in range(3):
+            assert err_maxnorm(outs[k].cpu().numpy(), conv(np.ascontiguousarray(L), Ks[k])) <= TOL_FP32
+        assert torch.isnan(store[:, :, shape[1]:]).all(), "wrote outside the output rows"
+        for s in specs:
+            lp.lp_spectrum_release(ctx, s)
+
+
+def test_single_row_and_column_maps(ctx):
+    g = np.random.default_rng(13)
+    K = g.uniform(0.1, 1.0, (5, 5))
+    for shape in [(1, 60), (60, 1), (1, 1)]:
+        L = g.lognormal(0.0, 1.0, shape).astype(np.float32)
+        (B,) = run_map(ctx, L, [K], mode=lp.LP_OUT_FULL)
+        assert err_maxnorm(B, oracle.conv_full(L, K)) <= TOL_FP32
+
+
+def test_zero_map_gives_zero(ctx):
+    K = synth.psf_power_exp(21, 1.0, 0.25, 1.25, 40.0)
+    (B,) = run_map(ctx, np.zeros((50, 70), np.float32), [K])
+    assert np.all(B == 0.0)
+
+
+def test_multiclass_eq4(ctx):
+    g = np.random.default_rng(14)
+    Ls = [g.lognormal(0.0, 1.0, (60, 75)).astype(np.float32) for _ in range(3)]
+    Ks = [synth.psf_power_exp(15, 1.0, 0.25, p, 40.0) for p in (1.0, 1.5, 2.0)]
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=60, max_w=75) for K in Ks]
+    out = torch.empty((60, 75), dtype=torch.float32, device=DEV)
+    lp.lp_map_multiclass(ctx, [dev(x) for x in Ls], specs, out)
+    lp.lp_sync_status(ctx)
+    ii, jj = np.meshgrid(np.arange(60), np.arange(75), indexing="ij")
+    ref = oracle.conv_multiclass_points_same(Ls, Ks, ii, jj).reshape(60, 75)
+    assert err_maxnorm(out.cpu().numpy(), ref) <= TOL_FP32
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+
+
+def test_host_entry_point_matches_device(ctx):
+    wl = synth.WORKLOADS["map256_psf101"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    s = lp.lp_kernel_spectrum(ctx, dev(K), max_h=256, max_w=256)
+    out_d = torch.empty((256, 256), dtype=torch.float32, device=DEV)
+    lp.lp_map(ctx, dev(L), [s], [out_d])
+    out_h = torch.empty((256, 256), dtype=torch.float32).pin_memory()
+    L_h = torch.from_numpy(L).pin_memory()
+    lp.lp_map_host(ctx, L_h, [s], [out_h])
+    lp.lp_sync_status(ctx)
+    assert torch.equal(out_h, out_d.cpu())
+    lp.lp_spectrum_release(ctx, s)
+
+
+# --- full-size workloads, sampled against the oracle -------------------------
+
+def _sampled_check(L, K, B, seed, n=4096, top=64):
+    H, W = L.shape
+    ii, jj = synth.sample_pixels(H, W, n, seed)
+    flat = np.argpartition(B.ravel(), -top)[-top:]
+    ii = np.concatenate([ii, flat // W])
+    jj = np.concatenate([jj, flat % W])
+    ref = oracle.conv_points_same(L, K, ii, jj)
+    return err_maxnorm(B[ii, jj], ref)
+
+
+def test_map4096_psf541_sampled(ctx):
+    wl = synth.WORKLOADS["map4096_psf541"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_map(ctx, L, [K])
+    assert _sampled_check(L, K, B, wl.seed + 100) <= TOL_FP32
+
+
+def test_map8192_psf601x16_batched_sampled(ctx):
+    wl = synth.WORKLOADS["map8192_psf601x16"]
+    L, Ks = wl.radiance(), wl.psfs()
+    Bs = run_map(ctx, L, Ks)
+    for k, (K, B) in enumerate(zip(Ks, Bs)):
+        assert _sampled_check(L, K, B, wl.seed + 100 + k, n=256, top=16) <= TOL_FP32, k
+
+
+def test_map16384_psf801_sampled(ctx):
+    wl = synth.WORKLOADS["map16384_psf801"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_map(ctx, L, [K])
+    assert _sampled_check(L, K, B, wl.seed + 100) <= TOL_FP32
+
+
+# --- cache, budget, validation, bounded waits ---------------------------------
+
+def test_spectrum_cache_refcount(ctx):
+    K = dev(synth.psf_power_exp(11, 1.0, 0.25, 1.25, 40.0))
+    a = lp.lp_kernel_spectrum(ctx, K, max_h=64, max_w=64)
+    b = lp.lp_kernel_spectrum(ctx, K, max_h=64, max_w=64)
+    c = lp.lp_kernel_spectrum(ctx, K, pad_ny=96, pad_nx=96)
+    assert a == b and a != c
+    lp.lp_spectrum_release(ctx, a)
+    lp.lp_spectrum_release(ctx, b)
+    lp.lp_spectrum_release(ctx, c)
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_spectrum_release(ctx, a)
+    assert e.value.status == lp.LP_ERR_INVALID
+
+
+def test_budget_refuses_oversized_spectrum():
+    c = lp.lp_create(0, 4 << 20)
+    try:
+        K = dev(synth.psf_power_exp(541, 0.742, 0.1, 1.25, 80.0))
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_kernel_spectrum(c, K, max_h=4096, max_w=4096)
+        assert e.value.status == lp.LP_ERR_OOM
+        assert lp.lp_bytes_in_use(c) < 4 << 20
+    finally:
+        lp.lp_destroy(c)
+
+
+def test_invalid_arguments(ctx):
+    g = np.random.default_rng(15)
+    L = dev(g.uniform(0, 1, (40, 50)).astype(np.float32))
+    K = dev(g.uniform(0, 1, (9, 9)))
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_kernel_spectrum(ctx, dev(g.uniform(0, 1, (8, 9))), max_h=40, max_w=50)
+    assert e.value.status == lp.LP_ERR_INVALID
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_kernel_spectrum(ctx, K, pad_ny=97, pad_nx=96)       # 97 not a built length
+    assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=50, prec=lp.LP_PREC_SPLIT_BF16)
+    assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    s_small = lp.lp_kernel_spectrum(ctx, K, pad_ny=45, pad_nx=64)  # 45 < 40 + 9 - 1
+    out = torch.empty((40, 50), dtype=torch.float32, device=DEV)
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_map(ctx, L, [s_small], [out])
+    assert e.value.status == lp.LP_ERR_INVALID
+    s = lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=50)
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_map(ctx, L, [s], [L])                               # in place
+    assert e.value.status == lp.LP_ERR_INVALID
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_map(ctx, L, [s], [out], prec=lp.LP_PREC_SPLIT_FP16)
+    assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    st = lp.call_status("lp_map", ctx, L.data_ptr(), 40, 50, 30, None, 1, None, 50, 0, 0, None)
+    assert st == lp.LP_ERR_INVALID
+    lp.lp_spectrum_release(ctx, s)
+    lp.lp_spectrum_release(ctx, s_small)
+
+
+def test_sync_status_wait_is_bounded(ctx):
+    wl = synth.WORKLOADS["map4096_psf541"]
+    L = dev(wl.radiance())
+    s = lp.lp_kernel_spectrum(ctx, dev(wl.psfs()[0]), max_h=4096, max_w=4096)
+    out = torch.empty_like(L)
+    lp.lp_sync_status(ctx)
+    for _ in range(40):
+        lp.lp_map(ctx, L, [s], [out])
+    assert lp.lp_sync_status_code(ctx, timeout_ms=0) == lp.LP_ERR_TIMEOUT
+    assert lp.lp_sync_status_code(ctx, timeout_ms=-1) == lp.LP_OK
+    lp.lp_spectrum_release(ctx, s)

@@ -1,0 +1,84 @@
+"""Host-side checks of the C-ABI library: it loads, exports every entry point
+declared in include/lp.h, and its size table and errors work without a GPU.
+No compute call is made here."""
+
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1907_02891_gb300 import build, lp
+    if not os.path.exists(lp.LIB_PATH):
+        build.build()
+    return lp.load_library()
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            with open(os.path.join(ROOT, "include", f)) as fh:
+                text = fh.read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lp_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1907_02891_gb300 import lp
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(lp.EXPORTS) <= set(declared)
+
+
+def test_supported_sizes_cover_the_workloads(lib):
+    from paper_1907_02891_gb300 import build, lp
+    sizes = lp.supported_sizes()
+    assert sizes == sorted(sizes) and len(sizes) == len(build.SIZES)
+    for n in sizes:
+        f = build.choose_plan(n)
+        assert all(r in build.RADICES for r in f)
+        p = 1
+        for r in f:
+            p *= r
+        assert p == n
+        m = n
+        for q in (2, 3, 5, 7):
+            while m % q == 0:
+                m //= q
+        assert m == 1, f"{n} is not 7-smooth"
+    # padded sizes of the workloads: map + PSF - 1 -> smallest supported
+    assert lp.lp_supported_size(356) == 360
+    assert lp.lp_supported_size(4636) == 4704
+    assert lp.lp_supported_size(8792) == 8820
+    assert lp.lp_supported_size(17184) == 17280
+    assert lp.lp_supported_size(10 ** 6) == -1
+    assert lp.lp_supported_size_at(-1) == -1
+
+
+def test_workspace_model(lib):
+    from paper_1907_02891_gb300 import lp
+    # T: 2353 x 4096 + U: 2353 x 4096 complex64 (+ alignment slack)
+    b = lp.lp_map_workspace_bytes(4096, 4096, 4704, 4704, 541, 541, 1)
+    assert b == 8 * 2353 * (4096 + 4096) + 256
+    assert lp.lp_map_workspace_bytes(0, 4096, 4704, 4704, 541, 541, 1) == 0
+
+
+def test_no_gpu_errors_are_reported_not_raised(lib):
+    import ctypes
+    from paper_1907_02891_gb300 import lp
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = ctypes.c_void_p()
+    st = lib.lp_create(ctypes.byref(ctx), 0, 0)
+    assert st == lp.LP_ERR_CUDA and ctx.value is None
+    assert b"no CUDA device" in lib.lp_last_error()
+    assert lib.lp_create(None, 0, 0) == lp.LP_ERR_INVALID
