@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Fourier-domain light-pollution map.
+
+One step = one call of the C-ABI map (row forward transform, column
+transform with the PSF-spectrum product, row inverse transform and crop)
+over a synthetic radiance map resident in HBM, with the PSF spectrum cached.
+The L2 cache is flushed (256 MiB write) between timed steps, outside the
+timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, host cores
+
+Metric: output Mpix/s per PSF map = H * W * n_spectra * steps / time.
+Multi-GPU (torchrun): every rank maps its own radiance map (independent
+units, no data exchange); value = all ranks' pixels / max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output Mpix/s per kernel map"
+UNIT = "Mpix/s"
+DEFAULT_WORKLOAD = "map4096_psf541"
+FALLBACK_HBM_GBS = 6800.0
+PASSES = ("p1_rows", "p2_cols", "p3_rows")
+KERNEL_SOURCES = ("paper_1907_02891_gb300/csrc/fft_core.cuh",
+                  "paper_1907_02891_gb300/csrc/conv_kernels.cuh",
+                  "paper_1907_02891_gb300/build.py")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# byte model (algorithmic bytes per pass, complex64 intermediates)
+# ----------------------------------------------------------------------------
+
+def pass_bytes(H, W, ny, nx, n, s_k):
+    nc = nx // 2 + 1
+    t = 8 * H * nc
+    return {
+        "p1_rows": 4 * H * W + t,                          # read L, write T
+        "p2_cols": t + n * (s_k * ny * nc + t),            # read T, K^, write U
+        "p3_rows": n * (t + 4 * H * W),                    # read U, write B
+    }
+
+
+def kernel_source_sha():
+    h = hashlib.sha1()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dram_traffic(kernel, workload):
+    """ncu dram bytes per launch, if captured for the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)[workload][kernel]
+    except Exception:
+        return None
+    if rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# clock sampling during the timed region
+# ----------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9 or not f[0].isdigit() or int(f[0]) != self.gpu:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (baseline arm and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_rate(L, K, seconds, seed):
+    """Time the FP64 direct sum on seeded pixels for about `seconds`."""
+    import oracle
+    import synth
+    H, W = L.shape
+    ii, jj = synth.sample_pixels(H, W, 256, seed)
+    t0 = time.perf_counter()
+    oracle.conv_points_same(L, K, ii, jj)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(2_000_000, max(256, 256 * seconds / dt)))
+    ii, jj = synth.sample_pixels(H, W, n, seed + 1)
+    t0 = time.perf_counter()
+    oracle.conv_points_same(L, K, ii, jj)
+    dt = time.perf_counter() - t0
+    return n / dt / 1e6, n, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, rank 0 only."""
+    import numpy as np
+    import synth
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[args.workload]
+    L = wl.radiance()
+    Ks = wl.psfs()
+    K = Ks[0]
+    # per-step sample sized so that warmup + steps take about two minutes
+    rate, _, _, cores = oracle_rate(L, K, 2.0, wl.seed + 7)
+    per_step = max(16, int(rate * 1e6 * 120.0 / max(1, args.steps + args.warmup)))
+    import oracle
+    H, W = L.shape
+    tot_px, tot_s = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        ii, jj = synth.sample_pixels(H, W, per_step, wl.seed + 1000 + s)
+        t0 = time.perf_counter()
+        for Kk in Ks:
+            oracle.conv_points_same(L, Kk, ii, jj)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            tot_px += per_step * len(Ks)
+            tot_s += dt
+    value = tot_px / tot_s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} seeded output pixels per step per PSF "
+                                   f"({len(Ks)} PSF) of the {H}x{W} map, FP64 direct sum"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, pad):
+    c = {"workload": wl.name, "map": f"{wl.H}x{wl.W}", "psf": f"{wl.psf_side}x{wl.psf_side}",
+         "n_psf": len(wl.psf_params), "pixel_km": wl.px_km,
+         "l2": "flushed between steps (256 MiB write, outside the timed events)"}
+    if pad is not None:
+        c["padded"] = f"{pad[0]}x{pad[1]}"
+    return c
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import synth
+    from paper_1907_02891_gb300 import lp
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = synth.WORKLOADS[args.workload]
+    H, W = wl.H, wl.W
+    L_host = wl.radiance()
+    Ks = wl.psfs()
+    n = len(Ks)
+
+    ctx = lp.lp_create(local_rank)
+    stream = torch.cuda.current_stream()
+    L = torch.from_numpy(L_host).to(dev)
+    t0 = time.perf_counter()
+    specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), max_h=H, max_w=W)
+             for K in Ks]
+    torch.cuda.synchronize()
+    s0_ms = 1e3 * (time.perf_counter() - t0) / n
+    info = lp.lp_spectrum_info(specs[0])
+    ny, nx = info["ny"], info["nx"]
+    s_k = 4 if info["is_real"] else 8
+    outs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(n)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        lp.lp_map(ctx, L, specs, outs)
+    lp.lp_sync_status(ctx)
+    lp.lp_set_pass_timing(ctx, True)
+    lp.lp_get_pass_timing(ctx)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        lp.lp_map(ctx, L, specs, outs)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    wall_s = time.perf_counter() - w0
+    clk = clocks.stop()
+    lp.lp_sync_status(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    dev_ms = float(sum(step_ms))
+    passes = lp.lp_get_pass_timing(ctx)
+    lp.lp_set_pass_timing(ctx, False)
+    if dist:
+        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    px = float(H) * W * n * args.steps * world
+    value = px / (dev_ms / 1e3) / 1e6
+
+    # roofline of the dominant pass
+    model = pass_bytes(H, W, ny, nx, n, s_k)
+    dom = max(PASSES, key=lambda p: passes[p][0])
+    ms_tot, launches = passes[dom]
+    per_launch_s = ms_tot / 1e3 / max(1, launches)
+    per_launch_bytes = model[dom] * (args.steps / max(1, launches))
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = dram_traffic(dom, wl.name)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        Lh = torch.from_numpy(L_host).pin_memory()
+        oh = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(n)]
+        for _ in range(3):
+            lp.lp_map_host(ctx, Lh, specs, oh)
+        lp.lp_sync_status(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            lp.lp_map_host(ctx, Lh, specs, oh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": float(H) * W * n * args.e2e_steps * world / (e_ms / 1e3) / 1e6,
+               "unit": UNIT, "h2d_bytes_per_step": 4 * H * W,
+               "d2h_bytes_per_step": 4 * H * W * n, "steps": args.e2e_steps,
+               "host_memory": "pinned"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, npx, secs, cores = oracle_rate(L_host, Ks[0], args.cpu_seconds, wl.seed + 7)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{npx} seeded output pixels of the {H}x{W} map with the first "
+                         f"{wl.psf_side}x{wl.psf_side} PSF, FP64 direct sum, {secs:.1f} s"}
+
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+    lp.lp_destroy(ctx)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(wl, (ny, nx)),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": per_launch_bytes},
+        "passes": {p: {"ms_per_launch": passes[p][0] / max(1, passes[p][1]),
+                       "launches": passes[p][1],
+                       "algorithmic_gbs": model[p] * args.steps / max(1, passes[p][1]) /
+                       (passes[p][0] / 1e3 / max(1, passes[p][1])) / 1e9}
+                   for p in PASSES},
+        "whole_step_gbs": sum(model.values()) / (dev_ms / args.steps / 1e3) / 1e9 / world,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": sum(passes[p][1] for p in PASSES),
+        "spectrum_build_ms": s0_ms, "wall_s": wall_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as td
+            td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

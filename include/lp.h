@@ -189,6 +189,17 @@ size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int 
  */
 lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
 
+/*
+ * Pass timing (tracing).  While enabled, every map call records CUDA events
+ * around each of its kernel passes on its own stream:
+ *   pass 0 = row forward transform (P1), 1 = column transform with the
+ *   spectrum product (P2), 2 = row inverse transform and crop (P3).
+ * lp_get_pass_timing waits for the recorded work, returns the summed
+ * milliseconds and launch counts per pass (arrays of 3) and clears them.
+ */
+lp_status lp_set_pass_timing(lp_ctx* ctx, int enable);
+lp_status lp_get_pass_timing(lp_ctx* ctx, double* ms, int* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,7 +96,7 @@ def plan_table() -> Dict[int, dict]:
     for n in SIZES:
         r = choose_plan(n)
         t = threads_for(n, r)
-        smem = 2 * spad_size(n) * 4
+        smem = 8 * (n + n // 16 + 16)   # upper bound of the padded extent
         if smem > SMEM_LIMIT:
             raise ValueError(f"length {n} needs {smem} bytes of shared memory")
 
@@ -123,7 +123,7 @@ namespace {{
 constexpr int kN = {n};
 using P = Plan<kN, Seq<{seq}>>;
 constexpr int kF1 = {f1}, kF3 = {f3};
-constexpr int kSmem = P::SMEM_FLOATS * 4;
+constexpr int kSmem = P::SMEM_BYTES;
 
 template <class K>
 cudaError_t attr(K k, int bytes)
@@ -135,8 +135,10 @@ cudaError_t set_attrs()
 {{
     cudaError_t e;
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, true>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, true>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_multiclass<P, kN, false>, kSmem)) != cudaSuccess) return e;
     return attr(p3_rows<P, kN, kF3>, kF3 * kSmem);
@@ -150,8 +152,11 @@ cudaError_t p1(const P1Args& a, int blocks, cudaStream_t s)
 
 cudaError_t p2(const P2Args& a, bool kreal, int blocks, cudaStream_t s)
 {{
-    if (kreal) p2_cols<P, kN, true><<<blocks, P::T, kSmem, s>>>(a);
-    else p2_cols<P, kN, false><<<blocks, P::T, kSmem, s>>>(a);
+    const bool multi = a.nspec > 1;
+    if (kreal && multi) p2_cols<P, kN, true, true><<<blocks, P::T, kSmem, s>>>(a);
+    else if (kreal) p2_cols<P, kN, true, false><<<blocks, P::T, kSmem, s>>>(a);
+    else if (multi) p2_cols<P, kN, false, true><<<blocks, P::T, kSmem, s>>>(a);
+    else p2_cols<P, kN, false, false><<<blocks, P::T, kSmem, s>>>(a);
     return cudaGetLastError();
 }}
 

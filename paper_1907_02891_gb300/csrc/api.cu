@@ -277,6 +277,11 @@ extern "C" void lp_destroy(lp_ctx* ctx)
     ctx->plans.clear();
     lp_ctx_free(ctx, ctx->staging, ctx->staging_bytes);
     lp_ctx_free(ctx, ctx->d_err, 64);
+    for (auto& pe : ctx->tim_pending) {
+        cudaEventDestroy(pe.start);
+        cudaEventDestroy(pe.stop);
+    }
+    for (auto ev : ctx->tim_pool) cudaEventDestroy(ev);
     delete ctx;
 }
 
@@ -558,7 +563,9 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     a1.ncols = d.ncols;
     a1.tw = px->fwd;
     const int f1 = px->k->f1;
+    int tok = lp_pass_begin(ctx, 0, st);
     CUDA_TRY(px->k->p1(a1, (npairs + f1 - 1) / f1, st));
+    lp_pass_end(ctx, tok, st);
 
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
@@ -586,7 +593,9 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
             a2.ncols = d.ncols;
             a2.twf = py->fwd;
             a2.twi = py->rev;
+            tok = lp_pass_begin(ctx, 1, st);
             CUDA_TRY(py->k->p2(a2, kind != 0, d.ncols, st));
+            lp_pass_end(ctx, tok, st);
             k0 = k1;
         }
         P3Args a3;
@@ -602,7 +611,9 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         a3.ncols = d.ncols;
         a3.tw = px->rev;
         const int f3 = px->k->f3;
+        tok = lp_pass_begin(ctx, 2, st);
         CUDA_TRY(px->k->p3(a3, (a3.npairs + f3 - 1) / f3, cnt, st));
+        lp_pass_end(ctx, tok, st);
     }
     return LP_OK;
 }
@@ -793,5 +804,70 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a3.ncols = d.ncols;
     a3.tw = px->rev;
     CUDA_TRY(px->k->p3(a3, (a3.npairs + px->k->f3 - 1) / px->k->f3, 1, s));
+    return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pass timing
+// ---------------------------------------------------------------------------
+static cudaEvent_t pool_event(lp_ctx* ctx)
+{
+    if (!ctx->tim_pool.empty()) {
+        cudaEvent_t e = ctx->tim_pool.back();
+        ctx->tim_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+int lp_pass_begin(lp_ctx* ctx, int pass, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> g(ctx->tim_mu);
+    if (!ctx->timing) return -1;
+    PassEvent pe{pass, pool_event(ctx), pool_event(ctx)};
+    if (!pe.start || !pe.stop) return -1;
+    cudaEventRecord(pe.start, s);
+    ctx->tim_pending.push_back(pe);
+    return (int)ctx->tim_pending.size() - 1;
+}
+
+void lp_pass_end(lp_ctx* ctx, int token, cudaStream_t s)
+{
+    if (token < 0) return;
+    std::lock_guard<std::mutex> g(ctx->tim_mu);
+    if (token < (int)ctx->tim_pending.size()) cudaEventRecord(ctx->tim_pending[token].stop, s);
+}
+
+extern "C" lp_status lp_set_pass_timing(lp_ctx* ctx, int enable)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_set_pass_timing: NULL context");
+    std::lock_guard<std::mutex> g(ctx->tim_mu);
+    ctx->timing = enable != 0;
+    return LP_OK;
+}
+
+extern "C" lp_status lp_get_pass_timing(lp_ctx* ctx, double* ms, int* launches)
+{
+    if (!ctx || !ms || !launches) return lp_fail(LP_ERR_INVALID, "lp_get_pass_timing: NULL argument");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::mutex> g(ctx->tim_mu);
+    for (int i = 0; i < 3; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (auto& pe : ctx->tim_pending) {
+        CUDA_TRY(cudaEventSynchronize(pe.stop));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, pe.start, pe.stop));
+        if (pe.pass >= 0 && pe.pass < 3) {
+            ms[pe.pass] += t;
+            launches[pe.pass] += 1;
+        }
+        ctx->tim_pool.push_back(pe.start);
+        ctx->tim_pool.push_back(pe.stop);
+    }
+    ctx->tim_pending.clear();
     return LP_OK;
 }

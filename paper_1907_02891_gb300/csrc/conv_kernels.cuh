@@ -79,7 +79,12 @@ struct Plan {
     static constexpr int R0 = SeqInfo<Fwd>::first;   // first forward radix
     static constexpr int RL = SeqInfo<Fwd>::last;    // last forward radix
     static constexpr int T = ((N / SeqInfo<Fwd>::min_r) + 31) / 32 * 32;  // threads per FFT
-    static constexpr int SMEM_FLOATS = 2 * spad_size(N);
+    // shared memory (complex elements) of one transform: the larger padded
+    // extent of the forward and the reversed chain
+    static constexpr int SMEM_ELEMS = ChainExtent<Fwd>::value > ChainExtent<Inv>::value
+                                          ? ChainExtent<Fwd>::value
+                                          : ChainExtent<Inv>::value;
+    static constexpr int SMEM_BYTES = 8 * SMEM_ELEMS;
     static_assert(T <= 1024, "too many threads per transform");
 };
 
@@ -89,14 +94,13 @@ struct Plan {
 template <class P, int N, int F>
 __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 {
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
-    float* re = smem + f * P::SMEM_FLOATS;
-    float* im = re + spad_size(N);
+    float2* sm = smem2 + f * P::SMEM_ELEMS;
     const int pair = blockIdx.x * F + f;
     const int ra = 2 * pair, rb = ra + 1;
     const bool va = ra < a.H, vb = rb < a.H;
@@ -114,22 +118,20 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
         }
     }
     using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-    FwdChain::run(v, t, re, im, a.tw, [&](float2(&z)[RL], int j, bool act) {
+    FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[RL], int j, bool act) {
         __syncthreads();
         if (act) {
 #pragma unroll
-            for (int m = 0; m < RL; ++m) {
-                re[spad(j + m * NBL)] = z[m].x;
-                im[spad(j + m * NBL)] = z[m].y;
-            }
+            for (int m = 0; m < RL; ++m) sm[j + m * NBL] = z[m];
         }
         __syncthreads();
         if (pair < a.npairs) {
             float4* Tq = reinterpret_cast<float4*>(a.T);
             for (int c = t; c < a.ncols; c += T) {
                 const int cm = (c == 0) ? 0 : N - c;
-                const float zr = re[spad(c)], zi = im[spad(c)];
-                const float wr = re[spad(cm)], wi = -im[spad(cm)];
+                const float2 zc = sm[c], zm = sm[cm];
+                const float zr = zc.x, zi = zc.y;
+                const float wr = zm.x, wi = -zm.y;
                 // 2 X_a = Z[c] + conj Z[N-c] ; 2 X_b = -i (Z[c] - conj Z[N-c])
                 float4 o;
                 o.x = zr + wr;
@@ -145,14 +147,13 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 // ---------------------------------------------------------------------------
 // P2: per column forward FFT, spectrum product, inverse FFT, row crop.
 // ---------------------------------------------------------------------------
-template <class P, int N, bool KREAL>
+template <class P, int N, bool KREAL, bool MULTI>
 __global__ void __launch_bounds__(P::T) p2_cols(const P2Args a)
 {
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
-    float* re = smem;
-    float* im = smem + spad_size(N);
+    float2* sm = smem2;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
     const float2* col = a.T + (long long)c * a.ldT;
@@ -167,35 +168,45 @@ __global__ void __launch_bounds__(P::T) p2_cols(const P2Args a)
     }
     using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
     using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
-    FwdChain::run(v, t, re, im, a.twf, [&](float2(&fz)[RL], int j, bool act) {
-        for (int s = 0; s < a.nspec; ++s) {
-            float2 g[RL];
-            if (act) {
-                if constexpr (KREAL) {
-                    const float* kc = static_cast<const float*>(a.K[s]) + (long long)c * a.ldK;
+    auto product = [&](float2* g, const float2* fz, int s, int j) {
+        if constexpr (KREAL) {
+            const float* kc = static_cast<const float*>(a.K[s]) + (long long)c * a.ldK + j;
 #pragma unroll
-                    for (int m = 0; m < RL; ++m) {
-                        const float k = __ldg(kc + j + m * NBL);
-                        g[m] = make_float2(fz[m].x * k, fz[m].y * k);
-                    }
-                } else {
-                    const float2* kc = static_cast<const float2*>(a.K[s]) + (long long)c * a.ldK;
+            for (int m = 0; m < RL; ++m) {
+                const float k = __ldg(kc + m * NBL);
+                g[m] = make_float2(fz[m].x * k, fz[m].y * k);
+            }
+        } else {
+            const float2* kc = static_cast<const float2*>(a.K[s]) + (long long)c * a.ldK + j;
 #pragma unroll
-                    for (int m = 0; m < RL; ++m) g[m] = cmul(fz[m], __ldg(kc + j + m * NBL));
+            for (int m = 0; m < RL; ++m) g[m] = cmul(fz[m], __ldg(kc + m * NBL));
+        }
+    };
+    auto inverse = [&](float2(&g)[RL], int s, int j) {
+        float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
+        InvChain::run(g, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
+            if (act2) {
+#pragma unroll
+                for (int m = 0; m < R0; ++m) {
+                    int rr = j2 + m * NB0 - a.r0;
+                    if (rr < 0) rr += N;
+                    if (rr < a.Hout) Uc[rr] = o[m];
                 }
             }
-            float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
-            InvChain::run(g, j, re, im, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
-                if (act2) {
-#pragma unroll
-                    for (int m = 0; m < R0; ++m) {
-                        int rr = j2 + m * NB0 - a.r0;
-                        if (rr < 0) rr += N;
-                        if (rr < a.Hout) Uc[rr] = o[m];
-                    }
-                }
-                if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
-            });
+            if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+        });
+    };
+    FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
+        if constexpr (MULTI) {
+#pragma unroll 1
+            for (int s = 0; s < a.nspec; ++s) {
+                float2 g[RL];
+                if (act) product(g, fz, s, j);
+                inverse(g, s, j);
+            }
+        } else {
+            if (act) product(fz, fz, 0, j);
+            inverse(fz, 0, j);
         }
     });
 }
@@ -207,14 +218,13 @@ __global__ void __launch_bounds__(P::T) p2_cols(const P2Args a)
 template <class P, int N, int F>
 __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
 {
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int RI = SeqInfo<typename P::Inv>::first, NBI = N / RI;
     constexpr int RJ = SeqInfo<typename P::Inv>::last, NBJ = N / RJ;
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
-    float* re = smem + f * P::SMEM_FLOATS;
-    float* im = re + spad_size(N);
+    float2* sm = smem2 + f * P::SMEM_ELEMS;
     const int pair = blockIdx.x * F + f;
     const int sidx = blockIdx.y;
     const int ra = 2 * pair, rb = ra + 1;
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
         }
     }
     using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
-    InvChain::run(v, t, re, im, a.tw, [&](float2(&o)[RJ], int j, bool act) {
+    InvChain::run(v, t, sm, a.tw, [&](float2(&o)[RJ], int j, bool act) {
         if (act && live) {
             float* oa = a.out[sidx] + (long long)ra * a.ldo;
             float* ob = oa + a.ldo;
@@ -280,11 +290,10 @@ struct P2MArgs {
 template <class P, int N, bool KREAL>
 __global__ void __launch_bounds__(P::T) p2_multiclass(const P2MArgs a)
 {
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
-    float* re = smem;
-    float* im = smem + spad_size(N);
+    float2* sm = smem2;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
     using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
@@ -293,6 +302,7 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const P2MArgs a)
     float2 acc[RL];
 #pragma unroll
     for (int m = 0; m < RL; ++m) acc[m] = make_float2(0.f, 0.f);
+#pragma unroll 1
     for (int q = 0; q < a.nclass; ++q) {
         const float2* col = a.T[q] + (long long)c * a.ldT;
         float2 v[R0];
@@ -303,7 +313,7 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const P2MArgs a)
                 v[m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
             }
         }
-        FwdChain::run(v, t, re, im, a.twf, [&](float2(&fz)[RL], int j, bool act) {
+        FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
             if (act) {
                 if constexpr (KREAL) {
                     const float* kc = static_cast<const float*>(a.K[q]) + (long long)c * a.ldK;
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const P2MArgs a)
         __syncthreads();  // the next class's forward reuses re/im
     }
     float2* Uc = a.U + (long long)c * a.ldU;
-    InvChain::run(acc, t, re, im, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
+    InvChain::run(acc, t, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
         if (act2) {
 #pragma unroll
             for (int m = 0; m < R0; ++m) {

@@ -292,15 +292,48 @@ template <> struct SeqInfo<Seq<>> {
     static constexpr int first = 1, last = 1, min_r = 1 << 30, max_r = 0, product = 1, stages = 0;
 };
 
-// shared-memory index with one padding word per 32 (bank spreading)
-__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
-__host__ __device__ constexpr int spad_size(int n) { return n + (n >> 5) + 1; }
+// ---------------------------------------------------------------------------
+// Shared-memory exchange layout.  Complex values are stored interleaved
+// (one 64-bit access per element).  The exchange after a stage with group
+// size P = Ns * R inserts q padding elements after every group of P:
+//   padded(i) = i + q * (i / P).
+// The next stage reads x[j + m NB'] with NB' = N / R' a multiple of P, so
+// both sides stay "per-thread base + compile-time offset".  q is chosen so
+// that the 16 threads of each 64-bit access phase hit distinct bank pairs:
+// an odd element stride when Ns = 1, and consecutive banks across groups
+// (Ns R + q = Ns mod 16) otherwise.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pad_q(int Ns, int R)
+{
+    return Ns == 1 ? ((R % 2 == 0) ? 1 : 0) : (((Ns * (1 - R)) % 16) + 16) % 16;
+}
 
+// elements of shared memory one chain's exchanges touch
+template <int... Rs>
+__host__ __device__ constexpr int chain_extent()
+{
+    constexpr int S = sizeof...(Rs);
+    const int r[S] = {Rs...};
+    int n = 1;
+    for (int s = 0; s < S; ++s) n *= r[s];
+    int ext = n, Ns = 1;
+    for (int s = 0; s + 1 < S; ++s) {
+        const int P = Ns * r[s], q = pad_q(Ns, r[s]);
+        const int e = (n - 1) + q * ((n - 1) / P) + 1;
+        ext = e > ext ? e : ext;
+        Ns = P;
+    }
+    return ext;
+}
+template <class S> struct ChainExtent;
+template <int... Rs> struct ChainExtent<Seq<Rs...>> {
+    static constexpr int value = chain_extent<Rs...>();
+};
 
 // ---------------------------------------------------------------------------
 // Stage chain in FP32.  `run` takes the inputs of the first stage in v
 // (thread t holds x[t + m N/R] when t < N/R), runs every stage, exchanging
-// through shared memory (re, im) between stages, and hands the last stage's
+// through shared memory `sm` between stages, and hands the last stage's
 // outputs (thread t holds y[t + m N/R_last]) to `fin(v, t, active)`.
 // Every thread of the block must call it (it contains barriers).
 // ---------------------------------------------------------------------------
@@ -311,17 +344,21 @@ struct Chain<N, DIR, Ns, SIdx, Seq<R, Rest...>> {
     static constexpr int NB = N / R;
 
     template <class Fin>
-    __device__ __forceinline__ static void run(float2 (&v)[R], int t, float* re, float* im,
+    __device__ __forceinline__ static void run(float2 (&v)[R], int t, float2* sm,
                                                const TwChain& tw, Fin&& fin)
     {
         const bool act = t < NB;
         if (act) {
             if constexpr (Ns > 1) {
-                const int k = t % Ns;
                 const float2* tab = tw.p[SIdx];
+                // opaque to the optimiser: keeps the table loads inside loops
+                // that repeat a chain (n spectra, n classes) instead of hoisting
+                // every stage's twiddles into registers across iterations
+                asm volatile("" : "+l"(tab));
+                tab += t % Ns;
 #pragma unroll
                 for (int m = 1; m < R; ++m) {
-                    float2 w = __ldg(tab + (m - 1) * Ns + k);
+                    float2 w = __ldg(tab + (m - 1) * Ns);
                     if constexpr (DIR > 0) w.y = -w.y;
                     v[m] = cmul(v[m], w);
                 }
@@ -333,25 +370,24 @@ struct Chain<N, DIR, Ns, SIdx, Seq<R, Rest...>> {
         } else {
             constexpr int R2 = SeqInfo<Seq<Rest...>>::first;
             constexpr int NB2 = N / R2;
-            __syncthreads();  // earlier readers of re/im are done
+            constexpr int P = Ns * R;
+            constexpr int q = pad_q(Ns, R);
+            static_assert(NB2 % P == 0, "reader stride must be a multiple of the group size");
+            constexpr int rstride = NB2 + q * (NB2 / P);
+            __syncthreads();  // earlier readers of sm are done
             if (act) {
-                const int base = (t / Ns) * Ns * R + (t % Ns);
+                float2* w0 = sm + (t / Ns) * (P + q) + (t % Ns);
 #pragma unroll
-                for (int m = 0; m < R; ++m) {
-                    re[spad(base + m * Ns)] = v[m].x;
-                    im[spad(base + m * Ns)] = v[m].y;
-                }
+                for (int m = 0; m < R; ++m) w0[m * Ns] = v[m];
             }
             __syncthreads();
             float2 w[R2];
             if (t < NB2) {
+                const float2* r0 = sm + t + q * (t / P);
 #pragma unroll
-                for (int m = 0; m < R2; ++m) {
-                    w[m].x = re[spad(t + m * NB2)];
-                    w[m].y = im[spad(t + m * NB2)];
-                }
+                for (int m = 0; m < R2; ++m) w[m] = r0[m * rstride];
             }
-            Chain<N, DIR, Ns * R, SIdx + 1, Seq<Rest...>>::run(w, t, re, im, tw, fin);
+            Chain<N, DIR, Ns * R, SIdx + 1, Seq<Rest...>>::run(w, t, sm, tw, fin);
         }
     }
 };

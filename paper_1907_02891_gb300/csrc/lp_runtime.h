@@ -43,6 +43,11 @@ struct MapDims {
 
 struct ServeState;
 
+struct PassEvent {
+    int pass;
+    cudaEvent_t start, stop;
+};
+
 struct lp_spectrum {
     lp_ctx* ctx = nullptr;
     SpecKey key{};
@@ -65,6 +70,11 @@ struct lp_ctx {
     size_t staging_bytes = 0;
     int* d_err = nullptr;  // sticky device status word
     ServeState* serve = nullptr;
+    // pass timing
+    std::mutex tim_mu;
+    bool timing = false;
+    std::vector<PassEvent> tim_pending;
+    std::vector<cudaEvent_t> tim_pool;
 };
 
 lp_status lp_fail(lp_status st, const char* fmt, ...);
@@ -79,3 +89,7 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                         const MapDims& d, void* ws, cudaStream_t st);
 void lp_serve_shutdown(lp_ctx* ctx);
+// records the start of pass `pass` on stream s when timing is on; returns a
+// token for lp_pass_end (-1 when off)
+int lp_pass_begin(lp_ctx* ctx, int pass, cudaStream_t s);
+void lp_pass_end(lp_ctx* ctx, int token, cudaStream_t s);

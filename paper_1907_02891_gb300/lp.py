@@ -33,6 +33,7 @@ EXPORTS = (
     "lp_num_supported_sizes", "lp_supported_size_at", "lp_supported_size",
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
     "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
+    "lp_set_pass_timing", "lp_get_pass_timing",
 )
 
 
@@ -74,6 +75,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_map_multiclass": ([_vp, _vp, _i, _i, _i, _i, _vp, _vp, _i, _i, _i, _vp], _i),
         "lp_map_workspace_bytes": ([_i, _i, _i, _i, _i, _i, _i, _i], _sz),
         "lp_sync_status": ([_vp, _vp, _i], _i),
+        "lp_set_pass_timing": ([_vp, _i], _i),
+        "lp_get_pass_timing": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -236,3 +239,18 @@ def lp_sync_status_code(ctx: int, stream=None, timeout_ms: int = 60000) -> int:
 def call_status(name: str, *args) -> int:
     """Raw call of an entry point returning its lp_status (for error tests)."""
     return getattr(load_library(), name)(*args)
+
+
+PASS_NAMES = ("p1_rows", "p2_cols", "p3_rows")
+
+
+def lp_set_pass_timing(ctx: int, enable: bool) -> None:
+    _check(load_library().lp_set_pass_timing(ctx, 1 if enable else 0), "lp_set_pass_timing")
+
+
+def lp_get_pass_timing(ctx: int) -> dict:
+    """{pass name: (total ms, launches)} since the last call; waits for them."""
+    ms = (ctypes.c_double * 3)()
+    n = (_i * 3)()
+    _check(load_library().lp_get_pass_timing(ctx, ms, n), "lp_get_pass_timing")
+    return {PASS_NAMES[i]: (ms[i], n[i]) for i in range(3)}

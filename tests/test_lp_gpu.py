@@ -242,7 +242,7 @@ def test_spectrum_cache_refcount(ctx):
     K = dev(synth.psf_power_exp(11, 1.0, 0.25, 1.25, 40.0))
     a = lp.lp_kernel_spectrum(ctx, K, max_h=64, max_w=64)
     b = lp.lp_kernel_spectrum(ctx, K, max_h=64, max_w=64)
-    c = lp.lp_kernel_spectrum(ctx, K, pad_ny=96, pad_nx=96)
+    c = lp.lp_kernel_spectrum(ctx, K, pad_ny=120, pad_nx=96)
     assert a == b and a != c
     lp.lp_spectrum_release(ctx, a)
     lp.lp_spectrum_release(ctx, b)
