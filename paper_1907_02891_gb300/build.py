@@ -35,6 +35,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
 # radices the in-register DFTs are instantiated for (7-smooth, <= 32)
 RADICES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32)
 MAX_THREADS = 1024
+PF_UNITS = 2          # work units per block of the prefetching kernels
 SMEM_LIMIT = 227 * 1024
 
 # Supported transform lengths.  Every length is 7-smooth; the list covers
@@ -124,6 +125,9 @@ constexpr int kN = {n};
 using P = Plan<kN, Seq<{seq}>>;
 constexpr int kF1 = {f1}, kF3 = {f3};
 constexpr int kSmem = P::SMEM_BYTES;
+constexpr int kSmem2 = P::SMEM_BYTES + 8 * kN;   // + a parked column (batched / multi-class)
+constexpr long long kMaxSmem = 227 * 1024;
+constexpr int kUPB = {upb};   // work units per block of the prefetching kernels
 
 template <class K>
 cudaError_t attr(K k, int bytes)
@@ -131,45 +135,90 @@ cudaError_t attr(K k, int bytes)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }}
 
+// blocks of a prefetching launch: each block takes kUPB units
+inline int persistent_grid(int units) {{ return (units + kUPB - 1) / kUPB; }}
+
 cudaError_t set_attrs()
 {{
     cudaError_t e;
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, true, false>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, false, false>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, true>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, true>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_multiclass<P, kN, false>, kSmem)) != cudaSuccess) return e;
-    return attr(p3_rows<P, kN, kF3>, kF3 * kSmem);
+    if constexpr (kSmem2 <= kMaxSmem) {{
+        if ((e = attr(p2_cols<P, kN, true, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_cols<P, kN, false, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_multiclass<P, kN, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
+    }}
+    if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p1_rows_pf<P, kN, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, true, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, false, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
+    return attr(p3_rows_pf<P, kN, kUPB>, (int)kMaxSmem);
 }}
 
-cudaError_t p1(const P1Args& a, int blocks, cudaStream_t s)
+cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
-    p1_rows<P, kN, kF1><<<blocks, P::T * kF1, kF1 * kSmem, s>>>(a);
+    const long long sm = kSmem + p1_stage_bytes(a.Wst);
+    if (sm <= kMaxSmem) {{
+        p1_rows_pf<P, kN, kUPB><<<persistent_grid(a.npairs), P::T, sm, s>>>(a);
+    }} else {{
+        p1_rows<P, kN, kF1><<<(a.npairs + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
+    }}
     return cudaGetLastError();
 }}
 
-cudaError_t p2(const P2Args& a, bool kreal, int blocks, cudaStream_t s)
+cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 {{
     const bool multi = a.nspec > 1;
-    if (kreal && multi) p2_cols<P, kN, true, true><<<blocks, P::T, kSmem, s>>>(a);
-    else if (kreal) p2_cols<P, kN, true, false><<<blocks, P::T, kSmem, s>>>(a);
-    else if (multi) p2_cols<P, kN, false, true><<<blocks, P::T, kSmem, s>>>(a);
-    else p2_cols<P, kN, false, false><<<blocks, P::T, kSmem, s>>>(a);
-    return cudaGetLastError();
+    const long long sm = kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal);
+    if (!multi) {{
+        if (sm <= kMaxSmem) {{
+            if (kreal) p2_cols_pf<P, kN, true, kUPB><<<persistent_grid(a.ncols), P::T, sm, s>>>(a);
+            else p2_cols_pf<P, kN, false, kUPB><<<persistent_grid(a.ncols), P::T, sm, s>>>(a);
+        }} else {{
+            if (kreal) p2_cols<P, kN, true, false><<<a.ncols, P::T, kSmem, s>>>(a);
+            else p2_cols<P, kN, false, false><<<a.ncols, P::T, kSmem, s>>>(a);
+        }}
+        return cudaGetLastError();
+    }}
+    if constexpr (kSmem2 <= kMaxSmem) {{
+        if (kreal) p2_cols<P, kN, true, true><<<a.ncols, P::T, kSmem2, s>>>(a);
+        else p2_cols<P, kN, false, true><<<a.ncols, P::T, kSmem2, s>>>(a);
+        return cudaGetLastError();
+    }} else {{
+        // no room to park the forward column: one pass per spectrum
+        for (int i = 0; i < a.nspec; ++i) {{
+            P2Args b = a;
+            b.K[0] = a.K[i];
+            b.nspec = 1;
+            b.U = a.U + (long long)i * a.specU;
+            cudaError_t e = p2(b, kreal, s);
+            if (e != cudaSuccess) return e;
+        }}
+        return cudaSuccess;
+    }}
 }}
 
-cudaError_t p2m(const P2MArgs& a, bool kreal, int blocks, cudaStream_t s)
+cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 {{
-    if (kreal) p2_multiclass<P, kN, true><<<blocks, P::T, kSmem, s>>>(a);
-    else p2_multiclass<P, kN, false><<<blocks, P::T, kSmem, s>>>(a);
-    return cudaGetLastError();
+    if constexpr (kSmem2 <= kMaxSmem) {{
+        if (kreal) p2_multiclass<P, kN, true><<<a.ncols, P::T, kSmem2, s>>>(a);
+        else p2_multiclass<P, kN, false><<<a.ncols, P::T, kSmem2, s>>>(a);
+        return cudaGetLastError();
+    }} else {{
+        return cudaErrorNotSupported;
+    }}
 }}
 
-cudaError_t p3(const P3Args& a, int blocks, int nspec, cudaStream_t s)
+cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
-    p3_rows<P, kN, kF3><<<dim3(blocks, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
+    const long long sm = kSmem + p3_stage_bytes(a.ncols);
+    if (sm <= kMaxSmem) {{
+        p3_rows_pf<P, kN, kUPB><<<dim3(persistent_grid(a.npairs), nspec), P::T, sm, s>>>(a);
+    }} else {{
+        p3_rows<P, kN, kF3><<<dim3((a.npairs + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
+    }}
     return cudaGetLastError();
 }}
 }}  // namespace
@@ -206,6 +255,7 @@ def generate() -> List[str]:
     for n, p in table.items():
         r = list(p["radices"])
         text = _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=p["f1"], f3=p["f3"], ns=len(r),
+                               upb=PF_UNITS,
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

@@ -557,14 +557,15 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     a1.ldl = ldl;
     a1.H = h;
     a1.W = w;
+    a1.Wst = (w + 3) / 4 * 4;
+    a1.vec16 = ((reinterpret_cast<uintptr_t>(L) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
     a1.T = T;
     a1.ldT = d.ldT;
     a1.npairs = npairs;
     a1.ncols = d.ncols;
     a1.tw = px->fwd;
-    const int f1 = px->k->f1;
     int tok = lp_pass_begin(ctx, 0, st);
-    CUDA_TRY(px->k->p1(a1, (npairs + f1 - 1) / f1, st));
+    CUDA_TRY(px->k->p1(a1, st));
     lp_pass_end(ctx, tok, st);
 
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
@@ -594,7 +595,7 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
             a2.twf = py->fwd;
             a2.twi = py->rev;
             tok = lp_pass_begin(ctx, 1, st);
-            CUDA_TRY(py->k->p2(a2, kind != 0, d.ncols, st));
+            CUDA_TRY(py->k->p2(a2, kind != 0, st));
             lp_pass_end(ctx, tok, st);
             k0 = k1;
         }
@@ -610,9 +611,8 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         a3.Wout = d.Wout;
         a3.ncols = d.ncols;
         a3.tw = px->rev;
-        const int f3 = px->k->f3;
         tok = lp_pass_begin(ctx, 2, st);
-        CUDA_TRY(px->k->p3(a3, (a3.npairs + f3 - 1) / f3, cnt, st));
+        CUDA_TRY(px->k->p3(a3, cnt, st));
         lp_pass_end(ctx, tok, st);
     }
     return LP_OK;
@@ -758,12 +758,14 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
         a1.ldl = ldl;
         a1.H = h;
         a1.W = w;
+        a1.Wst = (w + 3) / 4 * 4;
+        a1.vec16 = ((reinterpret_cast<uintptr_t>(L[t]) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
         a1.T = Tb + (size_t)t * d.ncols * d.ldT;
         a1.ldT = d.ldT;
         a1.npairs = npairs;
         a1.ncols = d.ncols;
         a1.tw = px->fwd;
-        CUDA_TRY(px->k->p1(a1, (npairs + px->k->f1 - 1) / px->k->f1, s));
+        CUDA_TRY(px->k->p1(a1, s));
     }
     // the real-spectrum kernel needs every class's spectrum real
     bool all_real = true;
@@ -790,7 +792,14 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a2.ncols = d.ncols;
     a2.twf = py->fwd;
     a2.twi = py->rev;
-    CUDA_TRY(py->k->p2m(a2, all_real, d.ncols, s));
+    {
+        const cudaError_t e = py->k->p2m(a2, all_real, s);
+        if (e == cudaErrorNotSupported)
+            return lp_fail(LP_ERR_UNSUPPORTED,
+                           "lp_map_multiclass: padded length %d leaves no shared memory for the "
+                           "class accumulator (supported up to about 14000)", s0->ny);
+        if (e != cudaSuccess) return lp_fail(LP_ERR_CUDA, "lp_map_multiclass: %s", cudaGetErrorString(e));
+    }
     P3Args a3;
     a3.U = U;
     a3.ldU = d.ldU;
@@ -803,7 +812,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a3.Wout = d.Wout;
     a3.ncols = d.ncols;
     a3.tw = px->rev;
-    CUDA_TRY(px->k->p3(a3, (a3.npairs + px->k->f3 - 1) / px->k->f3, 1, s));
+    CUDA_TRY(px->k->p3(a3, 1, s));
     return LP_OK;
 }
 

@@ -34,6 +34,8 @@ struct P1Args {
     const float* L;
     long long ldl;
     int H, W;
+    int Wst;    // staged row length (floats): W rounded up to a multiple of 4
+    int vec16;  // rows can be copied in 16-byte pieces (aligned base, ldl % 4 == 0, W % 4 == 0)
     float2* T;
     long long ldT;
     int npairs;  // ceil(H/2)
@@ -81,9 +83,11 @@ struct Plan {
     static constexpr int T = ((N / SeqInfo<Fwd>::min_r) + 31) / 32 * 32;  // threads per FFT
     // shared memory (complex elements) of one transform: the larger padded
     // extent of the forward and the reversed chain
-    static constexpr int SMEM_ELEMS = ChainExtent<Fwd>::value > ChainExtent<Inv>::value
-                                          ? ChainExtent<Fwd>::value
-                                          : ChainExtent<Inv>::value;
+    // (rounded up to an even count so that staging areas placed after it
+    // start on a 16-byte boundary, as cp.async of 16 bytes requires)
+    static constexpr int SMEM_ELEMS = ((ChainExtent<Fwd>::value > ChainExtent<Inv>::value
+                                            ? ChainExtent<Fwd>::value
+                                            : ChainExtent<Inv>::value) + 1) / 2 * 2;
     static constexpr int SMEM_BYTES = 8 * SMEM_ELEMS;
     static_assert(T <= 1024, "too many threads per transform");
 };
@@ -147,8 +151,61 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 // ---------------------------------------------------------------------------
 // P2: per column forward FFT, spectrum product, inverse FFT, row crop.
 // ---------------------------------------------------------------------------
+template <class P, int N, bool KREAL>
+__device__ __forceinline__ void p2_product_inverse(const P2Args& a, int c, int s, float2 (&g)[P::RL],
+                                                   int j, bool act, float2* sm)
+{
+    constexpr int R0 = P::R0, NB0 = N / R0;
+    constexpr int RL = P::RL, NBL = N / RL;
+    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
+    if (act) {
+        if constexpr (KREAL) {
+            const float* kc = static_cast<const float*>(a.K[s]) + (long long)c * a.ldK + j;
+#pragma unroll
+            for (int m = 0; m < RL; ++m) {
+                const float k = __ldg(kc + m * NBL);
+                g[m] = make_float2(g[m].x * k, g[m].y * k);
+            }
+        } else {
+            const float2* kc = static_cast<const float2*>(a.K[s]) + (long long)c * a.ldK + j;
+#pragma unroll
+            for (int m = 0; m < RL; ++m) g[m] = cmul(g[m], __ldg(kc + m * NBL));
+        }
+    }
+    float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
+    InvChain::run(g, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
+        if (act2) {
+#pragma unroll
+            for (int m = 0; m < R0; ++m) {
+                int rr = j2 + m * NB0 - a.r0;
+                if (rr < 0) rr += N;
+                if (rr < a.Hout) Uc[rr] = o[m];
+            }
+        }
+        if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+    });
+}
+
+// One spectrum of the batched column pass: the forward column is parked in
+// shared memory F (natural order); product with spectrum s, inverse, store.
+// Not inlined: as a loop body it would let the compiler keep the whole
+// inverse's constants and indices live across iterations.
+template <class P, int N, bool KREAL>
+__device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, const float2* F, float2* sm)
+{
+    constexpr int RL = P::RL, NBL = N / RL;
+    const int j = threadIdx.x;
+    const bool act = j < NBL;
+    float2 g[RL];
+    if (act) {
+#pragma unroll
+        for (int m = 0; m < RL; ++m) g[m] = F[j + m * NBL];
+    }
+    p2_product_inverse<P, N, KREAL>(a, c, s, g, j, act, sm);
+}
+
 template <class P, int N, bool KREAL, bool MULTI>
-__global__ void __launch_bounds__(P::T) p2_cols(const P2Args a)
+__global__ void __launch_bounds__(P::T) p2_cols(const __grid_constant__ P2Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -167,46 +224,16 @@ __global__ void __launch_bounds__(P::T) p2_cols(const P2Args a)
         }
     }
     using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
-    auto product = [&](float2* g, const float2* fz, int s, int j) {
-        if constexpr (KREAL) {
-            const float* kc = static_cast<const float*>(a.K[s]) + (long long)c * a.ldK + j;
-#pragma unroll
-            for (int m = 0; m < RL; ++m) {
-                const float k = __ldg(kc + m * NBL);
-                g[m] = make_float2(fz[m].x * k, fz[m].y * k);
-            }
-        } else {
-            const float2* kc = static_cast<const float2*>(a.K[s]) + (long long)c * a.ldK + j;
-#pragma unroll
-            for (int m = 0; m < RL; ++m) g[m] = cmul(fz[m], __ldg(kc + m * NBL));
-        }
-    };
-    auto inverse = [&](float2(&g)[RL], int s, int j) {
-        float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
-        InvChain::run(g, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
-            if (act2) {
-#pragma unroll
-                for (int m = 0; m < R0; ++m) {
-                    int rr = j2 + m * NB0 - a.r0;
-                    if (rr < 0) rr += N;
-                    if (rr < a.Hout) Uc[rr] = o[m];
-                }
-            }
-            if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
-        });
-    };
     FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
         if constexpr (MULTI) {
-#pragma unroll 1
-            for (int s = 0; s < a.nspec; ++s) {
-                float2 g[RL];
-                if (act) product(g, fz, s, j);
-                inverse(g, s, j);
+            float2* F = smem2 + P::SMEM_ELEMS;  // parked forward column
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < RL; ++m) F[j + m * NBL] = fz[m];
             }
+            for (int s = 0; s < a.nspec; ++s) p2_spectrum_pass<P, N, KREAL>(a, c, s, F, sm);
         } else {
-            if (act) product(fz, fz, 0, j);
-            inverse(fz, 0, j);
+            p2_product_inverse<P, N, KREAL>(a, c, 0, fz, j, act, sm);
         }
     });
 }
@@ -269,6 +296,254 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
 
 
 // ---------------------------------------------------------------------------
+// Prefetching variants.  Each block handles UPB work units (u, u + gridDim.x,
+// ...); while it transforms one unit, the input of the next one is copied
+// into a shared-memory staging area with cp.async (16-byte pieces where
+// aligned), so global-memory latency overlaps the butterflies instead of
+// stalling them.  cp.async.wait_group is a hardware wait: no spin loop is
+// involved.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+
+// staging bytes of the persistent kernels (host and device agree on these)
+__host__ __device__ constexpr long long p1_stage_bytes(int Wst) { return 8ll * Wst; }
+__host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long ldK, bool kreal)
+{
+    return 8ll * ldT + (kreal ? 4ll : 8ll) * ldK;
+}
+__host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll * ncols; }
+
+// Units per block of the prefetching kernels: the block handles units
+// blockIdx.x + i * gridDim.x for i < UPB, unrolled at compile time (a loop
+// back-edge makes the compiler keep ~70 more registers live per thread).
+template <class P, int N, int UPB>
+__global__ void __launch_bounds__(P::T) p1_rows_pf(const P1Args a)
+{
+    extern __shared__ float2 smem2[];
+    constexpr int T = P::T;
+    constexpr int R0 = P::R0, NB0 = N / R0;
+    constexpr int RL = P::RL, NBL = N / RL;
+    float2* sm = smem2;
+    float* st = reinterpret_cast<float*>(smem2 + P::SMEM_ELEMS);  // rows a, b: 2 x Wst floats
+    const int Wst = a.Wst;
+
+    auto prefetch = [&](int pair) {
+        if (pair >= a.npairs) return;
+        const int t = threadIdx.x;
+        for (int r = 0; r < 2; ++r) {
+            const int row = 2 * pair + r;
+            if (row >= a.H) continue;
+            const float* src = a.L + (long long)row * a.ldl;
+            float* dst = st + r * Wst;
+            if (a.vec16) {
+                for (int q = t; q < (a.W >> 2); q += T) cp_async16(dst + 4 * q, src + 4 * q);
+            } else {
+                for (int i = t; i < a.W; i += T) cp_async4(dst + i, src + i);
+            }
+        }
+        cp_async_commit();
+    };
+    auto unit = [&](int pair) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int t = threadIdx.x;
+        const bool vb = 2 * pair + 1 < a.H;
+        float2 v[R0];
+        if (t < NB0) {
+#pragma unroll
+            for (int m = 0; m < R0; ++m) {
+                const int col = t + m * NB0;
+                const bool in = col < a.W;
+                v[m].x = in ? st[col] : 0.f;
+                v[m].y = (in && vb) ? st[Wst + col] : 0.f;
+            }
+        }
+        __syncthreads();  // staging consumed
+        prefetch(pair + gridDim.x);
+        using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
+        FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[RL], int j, bool act) {
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < RL; ++m) sm[j + m * NBL] = z[m];
+            }
+            __syncthreads();
+            float4* Tq = reinterpret_cast<float4*>(a.T);
+            for (int c = t; c < a.ncols; c += T) {
+                const int cm = (c == 0) ? 0 : N - c;
+                const float2 zc = sm[c], zm = sm[cm];
+                float4 o;  // {2 X_a[c], 2 X_b[c]}
+                o.x = zc.x + zm.x;
+                o.y = zc.y - zm.y;
+                o.z = zc.y + zm.y;
+                o.w = -(zc.x - zm.x);
+                Tq[((long long)c * a.ldT) / 2 + pair] = o;
+            }
+        });
+    };
+    prefetch(blockIdx.x);
+    sfor<0, UPB>([&](auto I) {
+        const int pair = blockIdx.x + decltype(I)::value * gridDim.x;
+        if (pair < a.npairs) unit(pair);
+    });
+}
+
+// single spectrum; T column and K^ column staged
+template <class P, int N, bool KREAL, int UPB>
+__global__ void __launch_bounds__(P::T) p2_cols_pf(const P2Args a)
+{
+    extern __shared__ float2 smem2[];
+    constexpr int T = P::T;
+    constexpr int R0 = P::R0, NB0 = N / R0;
+    constexpr int RL = P::RL, NBL = N / RL;
+    constexpr int KW = KREAL ? 1 : 2;                    // floats per K^ element
+    float2* sm = smem2;
+    float2* tst = smem2 + P::SMEM_ELEMS;                 // ldT complex
+    float* kst = reinterpret_cast<float*>(tst + a.ldT);  // ldK floats or complex
+
+    auto prefetch_t = [&](int c) {
+        if (c >= a.ncols) return;
+        const float2* src = a.T + (long long)c * a.ldT;
+        for (int q = threadIdx.x; q < (int)(a.ldT >> 1); q += T) cp_async16(tst + 2 * q, src + 2 * q);
+        cp_async_commit();
+    };
+    auto prefetch_k = [&](int c) {
+        if (c >= a.ncols) return;
+        const float* src = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
+        for (int q = threadIdx.x; q < (int)((a.ldK * KW) >> 2); q += T) cp_async16(kst + 4 * q, src + 4 * q);
+        cp_async_commit();
+    };
+    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
+    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
+
+    auto unit = [&](int c) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int t = threadIdx.x;
+        float2 v[R0];
+        if (t < NB0) {
+#pragma unroll
+            for (int m = 0; m < R0; ++m) {
+                const int row = t + m * NB0;
+                v[m] = row < a.H ? tst[row] : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        prefetch_t(c + gridDim.x);
+        FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < RL; ++m) {
+                    if constexpr (KREAL) {
+                        const float k = kst[j + m * NBL];
+                        fz[m] = make_float2(fz[m].x * k, fz[m].y * k);
+                    } else {
+                        fz[m] = cmul(fz[m], reinterpret_cast<const float2*>(kst)[j + m * NBL]);
+                    }
+                }
+            }
+            __syncthreads();  // K^ staging consumed
+            prefetch_k(c + gridDim.x);
+            float2* Uc = a.U + (long long)c * a.ldU;
+            InvChain::run(fz, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
+                if (act2) {
+#pragma unroll
+                    for (int m = 0; m < R0; ++m) {
+                        int rr = j2 + m * NB0 - a.r0;
+                        if (rr < 0) rr += N;
+                        if (rr < a.Hout) Uc[rr] = o[m];
+                    }
+                }
+                if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+            });
+        });
+    };
+    prefetch_t(blockIdx.x);
+    prefetch_k(blockIdx.x);
+    sfor<0, UPB>([&](auto I) {
+        const int c = blockIdx.x + decltype(I)::value * gridDim.x;
+        if (c < a.ncols) unit(c);
+    });
+}
+
+template <class P, int N, int UPB>
+__global__ void __launch_bounds__(P::T) p3_rows_pf(const P3Args a)
+{
+    extern __shared__ float2 smem2[];
+    constexpr int T = P::T;
+    constexpr int RI = SeqInfo<typename P::Inv>::first, NBI = N / RI;
+    constexpr int RJ = SeqInfo<typename P::Inv>::last, NBJ = N / RJ;
+    float2* sm = smem2;
+    float4* ust = reinterpret_cast<float4*>(smem2 + P::SMEM_ELEMS);  // ncols x {A, B}
+    const int sidx = blockIdx.y;
+    const float4* Uq = reinterpret_cast<const float4*>(a.U + (long long)sidx * a.specU);
+    const long long ldq = a.ldU / 2;
+
+    auto prefetch = [&](int pair) {
+        if (pair >= a.npairs) return;
+        for (int k = threadIdx.x; k < a.ncols; k += T) cp_async16(ust + k, Uq + (long long)k * ldq + pair);
+        cp_async_commit();
+    };
+    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
+
+    auto unit = [&](int pair) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int t = threadIdx.x;
+        const int ra = 2 * pair, rb = ra + 1;
+        const bool vb = rb < a.Hout;
+        float2 v[RI];
+        if (t < NBI) {
+#pragma unroll
+            for (int m = 0; m < RI; ++m) {
+                const int k = t + m * NBI;
+                const bool lo = k < a.ncols;
+                float4 q = ust[lo ? k : N - k];
+                if (!vb) {
+                    q.z = 0.f;
+                    q.w = 0.f;
+                }
+                v[m] = lo ? make_float2(q.x - q.w, q.y + q.z) : make_float2(q.x + q.w, q.z - q.y);
+            }
+        }
+        __syncthreads();
+        prefetch(pair + gridDim.x);
+        InvChain::run(v, t, sm, a.tw, [&](float2(&o)[RJ], int j, bool act) {
+            if (act) {
+                float* oa = a.out[sidx] + (long long)ra * a.ldo;
+                float* ob = oa + a.ldo;
+#pragma unroll
+                for (int m = 0; m < RJ; ++m) {
+                    int cc = j + m * NBJ - a.c0;
+                    if (cc < 0) cc += N;
+                    if (cc < a.Wout) {
+                        oa[cc] = o[m].x;
+                        if (vb) ob[cc] = o[m].y;
+                    }
+                }
+            }
+        });
+    };
+    prefetch(blockIdx.x);
+    sfor<0, UPB>([&](auto I) {
+        const int pair = blockIdx.x + decltype(I)::value * gridDim.x;
+        if (pair < a.npairs) unit(pair);
+    });
+}
+
+// ---------------------------------------------------------------------------
 // P2 for Sec. 2.2 Eq. (4): several source classes, one PSF each.  The
 // forward column transform of each class's T is multiplied by its spectrum
 // and accumulated in registers; one inverse transform follows.
@@ -287,50 +562,70 @@ struct P2MArgs {
     TwChain twf, twi;
 };
 
+// One class of the Eq. (4) column pass: forward transform of the class's
+// column, product with its spectrum, accumulated into shared memory ACC
+// (natural order).  Not inlined, for the same reason as p2_spectrum_pass.
 template <class P, int N, bool KREAL>
-__global__ void __launch_bounds__(P::T) p2_multiclass(const P2MArgs a)
+__device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float2* ACC, float2* sm)
+{
+    constexpr int R0 = P::R0, NB0 = N / R0;
+    constexpr int RL = P::RL, NBL = N / RL;
+    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
+    const int t = threadIdx.x;
+    const float2* col = a.T[q] + (long long)c * a.ldT;
+    float2 v[R0];
+    if (t < NB0) {
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int row = t + m * NB0;
+            v[m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
+        }
+    }
+    FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
+        if (act) {
+            if constexpr (KREAL) {
+                const float* kc = static_cast<const float*>(a.K[q]) + (long long)c * a.ldK + j;
+#pragma unroll
+                for (int m = 0; m < RL; ++m) {
+                    const float k = __ldg(kc + m * NBL);
+                    float2& acc = ACC[j + m * NBL];
+                    acc.x += fz[m].x * k;
+                    acc.y += fz[m].y * k;
+                }
+            } else {
+                const float2* kc = static_cast<const float2*>(a.K[q]) + (long long)c * a.ldK + j;
+#pragma unroll
+                for (int m = 0; m < RL; ++m) {
+                    float2& acc = ACC[j + m * NBL];
+                    acc = cadd(acc, cmul(fz[m], __ldg(kc + m * NBL)));
+                }
+            }
+        }
+    });
+}
+
+template <class P, int N, bool KREAL>
+__global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2MArgs a)
 {
     extern __shared__ float2 smem2[];
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
     float2* sm = smem2;
+    float2* ACC = smem2 + P::SMEM_ELEMS;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
-    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
     using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
 
+    for (int i = t; i < N; i += blockDim.x) ACC[i] = make_float2(0.f, 0.f);
+    // every element of ACC is owned by one thread (j + m N/RL), so the
+    // accumulation needs no barrier; the chain's own barriers order sm
+    for (int q = 0; q < a.nclass; ++q) p2_class_pass<P, N, KREAL>(a, c, q, ACC, sm);
+    __syncthreads();
     float2 acc[RL];
+    const bool act = t < NBL;
+    if (act) {
 #pragma unroll
-    for (int m = 0; m < RL; ++m) acc[m] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int q = 0; q < a.nclass; ++q) {
-        const float2* col = a.T[q] + (long long)c * a.ldT;
-        float2 v[R0];
-        if (t < NB0) {
-#pragma unroll
-            for (int m = 0; m < R0; ++m) {
-                const int row = t + m * NB0;
-                v[m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
-            }
-        }
-        FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
-            if (act) {
-                if constexpr (KREAL) {
-                    const float* kc = static_cast<const float*>(a.K[q]) + (long long)c * a.ldK;
-#pragma unroll
-                    for (int m = 0; m < RL; ++m) {
-                        const float k = __ldg(kc + j + m * NBL);
-                        acc[m].x += fz[m].x * k;
-                        acc[m].y += fz[m].y * k;
-                    }
-                } else {
-                    const float2* kc = static_cast<const float2*>(a.K[q]) + (long long)c * a.ldK;
-#pragma unroll
-                    for (int m = 0; m < RL; ++m) acc[m] = cadd(acc[m], cmul(fz[m], __ldg(kc + j + m * NBL)));
-                }
-            }
-        });
-        __syncthreads();  // the next class's forward reuses re/im
+        for (int m = 0; m < RL; ++m) acc[m] = ACC[t + m * NBL];
     }
     float2* Uc = a.U + (long long)c * a.ldU;
     InvChain::run(acc, t, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {

@@ -27,10 +27,12 @@ struct SizeKernels {
     int f1, f3;          // transforms per block in the row passes
     int smem_bytes;      // dynamic shared memory of one transform
     cudaError_t (*set_attrs)();
-    cudaError_t (*p1)(const P1Args&, int blocks, cudaStream_t);
-    cudaError_t (*p2)(const P2Args&, bool kreal, int blocks, cudaStream_t);
-    cudaError_t (*p2m)(const P2MArgs&, bool kreal, int blocks, cudaStream_t);
-    cudaError_t (*p3)(const P3Args&, int blocks, int nspec, cudaStream_t);
+    // launchers: pick the persistent prefetching kernel when its shared
+    // memory fits, the one-unit-per-block kernel otherwise
+    cudaError_t (*p1)(const P1Args&, cudaStream_t);
+    cudaError_t (*p2)(const P2Args&, bool kreal, cudaStream_t);
+    cudaError_t (*p2m)(const P2MArgs&, bool kreal, cudaStream_t);
+    cudaError_t (*p3)(const P3Args&, int nspec, cudaStream_t);
 };
 
 // generated registry (one translation unit per size)
