@@ -177,6 +177,35 @@ lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T, int h, in
                             const lp_spectrum* const* spectra, float* out, int ldo,
                             lp_outmode mode, lp_precision prec, void* stream);
 
+/*
+ * lp_map without any allocation.  There is no counterpart in the paper: this
+ * is for callers that cannot let the library call cudaMalloc while they run
+ * -- a host framework that owns all device memory through its own pool and
+ * budget, or a latency-bound loop that cannot afford an allocation and the
+ * device synchronisation it brings.  Arguments, layouts, results and errors
+ * are those of lp_map, except:
+ *   - the intermediate spectra live in one static device array of
+ *     LP_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU loading this code
+ *     holds until the process exits; a map whose lp_map_workspace_bytes()
+ *     exceeds it is rejected with LP_ERR_INVALID (use lp_map instead);
+ *   - the spectra must exist already (their creation builds the FFT plans),
+ *     and pass timing must be off (it creates events); otherwise
+ *     LP_ERR_INVALID;
+ *   - the first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device current) and caches it: make
+ *     that first call before any stream capture;
+ *   - all calls share the array: calls whose work overlaps on the GPU race
+ *     and must be serialised by the caller.  Nothing needs clearing between
+ *     calls (every scratch element read is first written by the same call).
+ */
+#define LP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+lp_status lp_map_noalloc(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                         lp_outmode mode, lp_precision prec, void* stream);
+
+/* Size in bytes of the static scratch of lp_map_noalloc. */
+size_t lp_map_noalloc_scratch_bytes(void);
+
 /* Device bytes of workspace one lp_map call needs (0 if unsupported). */
 size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
                               lp_outmode mode);

@@ -33,7 +33,7 @@ EXPORTS = (
     "lp_num_supported_sizes", "lp_supported_size_at", "lp_supported_size",
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
     "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
-    "lp_set_pass_timing", "lp_get_pass_timing",
+    "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
 )
 
 
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_map_workspace_bytes": ([_i, _i, _i, _i, _i, _i, _i, _i], _sz),
         "lp_sync_status": ([_vp, _vp, _i], _i),
         "lp_set_pass_timing": ([_vp, _i], _i),
+        "lp_map_noalloc": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp], _i),
+        "lp_map_noalloc_scratch_bytes": ([], _sz),
         "lp_get_pass_timing": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
@@ -254,3 +256,25 @@ def lp_get_pass_timing(ctx: int) -> dict:
     n = (_i * 3)()
     _check(load_library().lp_get_pass_timing(ctx, ms, n), "lp_get_pass_timing")
     return {PASS_NAMES[i]: (ms[i], n[i]) for i in range(3)}
+
+
+def lp_map_noalloc(ctx: int, L, spectra: Sequence[int], out: Sequence, mode: int = LP_OUT_SAME,
+                   prec: int = LP_PREC_FP32, stream=None) -> None:
+    """lp_map with its scratch in the library's static device array: for
+    callers that cannot let the library allocate device memory while they
+    run.  Same arguments as lp_map; maps whose workspace exceeds
+    lp_map_noalloc_scratch_bytes() are rejected; concurrent calls race."""
+    h, w = L.shape
+    if L.stride(1) != 1 or any(o.stride(1) != 1 for o in out):
+        raise ValueError("rows must be contiguous")
+    ldo = out[0].stride(0)
+    if any(o.stride(0) != ldo for o in out):
+        raise ValueError("all outputs need the same row stride")
+    _check(load_library().lp_map_noalloc(ctx, L.data_ptr(), h, w, L.stride(0),
+                                         _ptr_array(spectra), len(spectra),
+                                         _ptr_array([o.data_ptr() for o in out]), ldo, mode,
+                                         prec, _stream_handle(stream)), "lp_map_noalloc")
+
+
+def lp_map_noalloc_scratch_bytes() -> int:
+    return load_library().lp_map_noalloc_scratch_bytes()
