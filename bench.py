@@ -52,6 +52,12 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU-oracle sample")
+    ap.add_argument("--mode", default="map", choices=["map", "serve"],
+                    help="map: the throughput line; serve: the request-scheduler run")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--load", type=float, default=0.7,
+                    help="offered load as a fraction of the measured back-to-back capacity")
+    ap.add_argument("--slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -370,6 +376,112 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# serving run
+# ----------------------------------------------------------------------------
+
+def run_serve(args, rank, world, local_rank):
+    """Poisson arrivals of map requests (tile side uniform on 256..8192, 1-8
+    PSFs of a bank of 8 cached 201^2 spectra) through the request scheduler;
+    p50/p99 latency and Mpix/s.  The same requests run back to back through
+    lp_map on one stream give the queue-alone reference."""
+    import threading
+    import numpy as np
+    import torch
+    import synth
+    from paper_1907_02891_gb300 import lp
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = lp.lp_create(local_rank)
+    bank = [torch.from_numpy(K).to(dev) for K in synth.serve_bank()]
+    sides = synth.SERVE_TILE_SIDES
+    spectra = {(s, i): lp.lp_kernel_spectrum(ctx, K, max_h=s, max_w=s)
+               for s in sides for i, K in enumerate(bank)}
+    maps = {s: torch.from_numpy(synth.radiance_map(s, s, max(4, s * s // 42000), synth.SERVE_SEED + s,
+                                                   lit_fraction=0.05)).to(dev) for s in sides}
+    ring = 12
+    outs = {s: [[torch.empty((s, s), device=dev) for _ in range(8)] for _ in range(ring)] for s in sides}
+    torch.cuda.synchronize()
+
+    def call_args(rq, r):
+        s = rq.side
+        return maps[s], [spectra[(s, i)] for i in rq.kernels], outs[s][r % ring][:len(rq.kernels)]
+
+    # capacity: the request mix back to back on one stream
+    probe = synth.request_stream(200, 1.0, seed=synth.SERVE_SEED + 99)
+    for rq in probe[:20]:
+        L, sp, o = call_args(rq, 0)
+        lp.lp_map(ctx, L, sp, o)
+    lp.lp_sync_status(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    px_probe = 0
+    for r, rq in enumerate(probe):
+        L, sp, o = call_args(rq, r)
+        lp.lp_map(ctx, L, sp, o)
+        px_probe += rq.side * rq.side * len(rq.kernels)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3
+    seq_mpix = px_probe / seq_s / 1e6
+    mean_service = seq_s / len(probe)
+    rate = args.load / mean_service
+
+    reqs = synth.request_stream(args.requests, rate)
+    lp.lp_serve_start(ctx, args.slots)
+    # warm every slot's workspace with the largest request
+    big = max(reqs, key=lambda q: (q.side, len(q.kernels)))
+    warm = [lp.lp_serve_submit(ctx, *call_args(big, k)) for k in range(args.slots)]
+    for t in warm:
+        lp.lp_serve_poll(ctx, t)
+    tickets = [None] * len(reqs)
+    lat = [None] * len(reqs)
+    done_t = [0.0] * len(reqs)
+
+    def poller():
+        for r in range(len(reqs)):
+            while tickets[r] is None:
+                time.sleep(20e-6)
+            lat[r] = lp.lp_serve_poll(ctx, tickets[r])
+            done_t[r] = time.perf_counter()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    for r, rq in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if rq.arrival_s > now:
+            time.sleep(rq.arrival_s - now)
+        if r >= ring:  # output ring: the request using these buffers must be done
+            while lat[r - ring] is None:
+                time.sleep(20e-6)
+        tickets[r] = lp.lp_serve_submit(ctx, *call_args(rq, r))
+    th.join()
+    clk = clocks.stop()
+    makespan = max(done_t) - t0
+    lp.lp_serve_stop(ctx)
+    px = sum(q.side * q.side * len(q.kernels) for q in reqs)
+    lat_ms = np.array(lat, dtype=np.float64)
+    line = {
+        "metric": "serve p50/p99 ms", "value": float(np.percentile(lat_ms, 50)),
+        "p99_ms": float(np.percentile(lat_ms, 99)), "unit": "ms", "higher_is_better": False,
+        "n_gpus": 1, "requests": len(reqs), "slots": args.slots, "offered_load": args.load,
+        "arrival_rate_hz": rate, "served_mpix_s": px / makespan / 1e6,
+        "back_to_back_mpix_s": seq_mpix, "mean_service_ms": 1e3 * mean_service,
+        "makespan_s": makespan, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve_tiles256-8192_bank8_psf201", "tile_sides": list(sides),
+                   "psf": "201x201", "kernels_per_request": "1-8", "arrivals": "Poisson"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    lp.lp_destroy(ctx)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +489,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "serve":
+        run_serve(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

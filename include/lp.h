@@ -219,6 +219,35 @@ size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int 
 lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
 
 /*
+ * Serving: continuous batching of map requests.  lp_serve_start creates
+ * n_slots CUDA streams (each with its own workspace) and a scheduler thread.
+ * lp_serve_submit validates a request exactly like lp_map (LP_OUT_* mode,
+ * FP32) and queues it; the scheduler starts queued requests in arrival order
+ * as soon as a slot is free and the request's workspace fits, next to the
+ * requests already running, into the serving capacity (the context's HBM
+ * budget minus what it holds at start, or 90 % of the free device memory
+ * when the context has no budget).  Requests admitted while others run
+ * overlap with them on the device.  A request larger than the capacity is
+ * refused at submission (LP_ERR_OOM); a full queue gives LP_ERR_BUSY.
+ * The caller keeps L, the spectra and out[] alive until the request is
+ * polled as finished.
+ *
+ * lp_serve_poll waits up to timeout_ms (< 0: no limit) for a ticket:
+ * LP_OK with the latency (submission to completion, milliseconds, host
+ * clock), LP_ERR_TIMEOUT if still pending, or the request's failure status.
+ * A finished ticket can be polled once.  lp_serve_stop drains the queue,
+ * waits for running requests and releases the slots.
+ */
+lp_status lp_serve_start(lp_ctx* ctx, int n_slots);
+lp_status lp_serve_submit(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                          const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                          lp_outmode mode, uint64_t* ticket);
+lp_status lp_serve_poll(lp_ctx* ctx, uint64_t ticket, int timeout_ms, double* latency_ms);
+lp_status lp_serve_stats(lp_ctx* ctx, uint64_t* completed, uint64_t* failed, int* queued,
+                         int* running);
+lp_status lp_serve_stop(lp_ctx* ctx);
+
+/*
  * Pass timing (tracing).  While enabled, every map call records CUDA events
  * around each of its kernel passes on its own stream:
  *   pass 0 = row forward transform (P1), 1 = column transform with the

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import hashlib
+import json
 import os
 import shutil
 import subprocess
@@ -92,26 +93,48 @@ def choose_plan(n: int) -> Tuple[int, ...]:
     return tuple(sorted(best[1], reverse=True))
 
 
+TUNED_JSON = os.path.join(HERE, "tuned_plans.json")
+
+
+def plan_table_entry(n: int) -> dict:
+    """Heuristic plan of one length (used when the autotuner has not
+    measured it)."""
+    r = choose_plan(n)
+    t = threads_for(n, r)
+    smem = 8 * (n + n // 16 + 16)   # upper bound of the padded extent
+    if smem > SMEM_LIMIT:
+        raise ValueError(f"length {n} needs {smem} bytes of shared memory")
+
+    def fits(f: int) -> bool:
+        return f * t <= MAX_THREADS and f * smem <= 100 * 1024
+
+    # transforms per block of the one-unit-per-block row kernels: two when
+    # they fit (32-byte column segments in T and U), one otherwise; more for
+    # tiny lengths
+    f = 1
+    for cand in (8, 4, 2):
+        if fits(cand) and (cand <= 2 or cand * t <= 256):
+            f = cand
+            break
+    return dict(radices=list(r), threads=t, f1=f, f3=f, smem=smem,
+                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True)
+
+
 def plan_table() -> Dict[int, dict]:
+    """Plan of every supported length: the autotuner's measured choice from
+    tuned_plans.json where there is one, the heuristic otherwise."""
+    tuned = {}
+    if os.path.exists(TUNED_JSON):
+        with open(TUNED_JSON) as fh:
+            tuned = json.load(fh)
     table = {}
     for n in SIZES:
-        r = choose_plan(n)
-        t = threads_for(n, r)
-        smem = 8 * (n + n // 16 + 16)   # upper bound of the padded extent
-        if smem > SMEM_LIMIT:
-            raise ValueError(f"length {n} needs {smem} bytes of shared memory")
-
-        def fits(f: int) -> bool:
-            return f * t <= MAX_THREADS and f * smem <= 100 * 1024
-
-        # transforms per block in the row passes: two when they fit (32-byte
-        # column segments in T and U), one otherwise; more for tiny lengths
-        f = 1
-        for cand in (8, 4, 2):
-            if fits(cand) and (cand <= 2 or cand * t <= 256):
-                f = cand
-                break
-        table[n] = dict(radices=r, threads=t, f1=f, f3=f, smem=smem)
+        e = plan_table_entry(n)
+        t = tuned.get(str(n))
+        if t:
+            e.update(radices=list(t["radices"]), threads=threads_for(n, t["radices"]),
+                     upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]))
+        table[n] = e
     return table
 
 
@@ -127,7 +150,11 @@ constexpr int kF1 = {f1}, kF3 = {f3};
 constexpr int kSmem = P::SMEM_BYTES;
 constexpr int kSmem2 = P::SMEM_BYTES + 8 * kN;   // + a parked column (batched / multi-class)
 constexpr long long kMaxSmem = 227 * 1024;
-constexpr int kUPB = {upb};   // work units per block of the prefetching kernels
+// tuned parameters of the prefetching kernels: work units per block and
+// minimum resident blocks per SM (register cap) per pass; spectrum staging
+constexpr int kUPB1 = {upb1}, kUPB2 = {upb2}, kUPB3 = {upb3};
+constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
+constexpr bool kKSTAGE = {kstage};
 
 template <class K>
 cudaError_t attr(K k, int bytes)
@@ -135,8 +162,8 @@ cudaError_t attr(K k, int bytes)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }}
 
-// blocks of a prefetching launch: each block takes kUPB units
-inline int persistent_grid(int units) {{ return (units + kUPB - 1) / kUPB; }}
+// blocks of a prefetching launch: each block takes upb units
+inline int persistent_grid(int units, int upb) {{ return (units + upb - 1) / upb; }}
 
 cudaError_t set_attrs()
 {{
@@ -151,17 +178,17 @@ cudaError_t set_attrs()
         if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
     }}
     if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p1_rows_pf<P, kN, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, true, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, false, kUPB>, (int)kMaxSmem)) != cudaSuccess) return e;
-    return attr(p3_rows_pf<P, kN, kUPB>, (int)kMaxSmem);
+    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE>, (int)kMaxSmem)) != cudaSuccess) return e;
+    return attr(p3_rows_pf<P, kN, kUPB3, kMINB3>, (int)kMaxSmem);
 }}
 
 cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
     const long long sm = kSmem + p1_stage_bytes(a.Wst);
     if (sm <= kMaxSmem) {{
-        p1_rows_pf<P, kN, kUPB><<<persistent_grid(a.npairs), P::T, sm, s>>>(a);
+        p1_rows_pf<P, kN, kUPB1, kMINB1><<<persistent_grid(a.npairs, kUPB1), P::T, sm, s>>>(a);
     }} else {{
         p1_rows<P, kN, kF1><<<(a.npairs + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
     }}
@@ -171,11 +198,13 @@ cudaError_t p1(const P1Args& a, cudaStream_t s)
 cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 {{
     const bool multi = a.nspec > 1;
-    const long long sm = kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal);
+    const long long sm = kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal, kKSTAGE);
     if (!multi) {{
         if (sm <= kMaxSmem) {{
-            if (kreal) p2_cols_pf<P, kN, true, kUPB><<<persistent_grid(a.ncols), P::T, sm, s>>>(a);
-            else p2_cols_pf<P, kN, false, kUPB><<<persistent_grid(a.ncols), P::T, sm, s>>>(a);
+            if (kreal)
+                p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
+            else
+                p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
         }} else {{
             if (kreal) p2_cols<P, kN, true, false><<<a.ncols, P::T, kSmem, s>>>(a);
             else p2_cols<P, kN, false, false><<<a.ncols, P::T, kSmem, s>>>(a);
@@ -215,7 +244,7 @@ cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
     const long long sm = kSmem + p3_stage_bytes(a.ncols);
     if (sm <= kMaxSmem) {{
-        p3_rows_pf<P, kN, kUPB><<<dim3(persistent_grid(a.npairs), nspec), P::T, sm, s>>>(a);
+        p3_rows_pf<P, kN, kUPB3, kMINB3><<<dim3(persistent_grid(a.npairs, kUPB3), nspec), P::T, sm, s>>>(a);
     }} else {{
         p3_rows<P, kN, kF3><<<dim3((a.npairs + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
     }}
@@ -255,7 +284,9 @@ def generate() -> List[str]:
     for n, p in table.items():
         r = list(p["radices"])
         text = _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=p["f1"], f3=p["f3"], ns=len(r),
-                               upb=PF_UNITS,
+                               upb1=p["upb"][0], upb2=p["upb"][1], upb3=p["upb"][2],
+                               minb1=p["minb"][0], minb2=p["minb"][1], minb3=p["minb"][2],
+                               kstage="true" if p["kstage"] else "false",
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

@@ -319,17 +319,17 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // staging bytes of the persistent kernels (host and device agree on these)
 __host__ __device__ constexpr long long p1_stage_bytes(int Wst) { return 8ll * Wst; }
-__host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long ldK, bool kreal)
+__host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long ldK, bool kreal, bool kstage)
 {
-    return 8ll * ldT + (kreal ? 4ll : 8ll) * ldK;
+    return 8ll * ldT + (kstage ? (kreal ? 4ll : 8ll) * ldK : 0ll);
 }
 __host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll * ncols; }
 
 // Units per block of the prefetching kernels: the block handles units
 // blockIdx.x + i * gridDim.x for i < UPB, unrolled at compile time (a loop
 // back-edge makes the compiler keep ~70 more registers live per thread).
-template <class P, int N, int UPB>
-__global__ void __launch_bounds__(P::T) p1_rows_pf(const P1Args a)
+template <class P, int N, int UPB, int MINB>
+__global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
@@ -400,9 +400,10 @@ __global__ void __launch_bounds__(P::T) p1_rows_pf(const P1Args a)
     });
 }
 
-// single spectrum; T column and K^ column staged
-template <class P, int N, bool KREAL, int UPB>
-__global__ void __launch_bounds__(P::T) p2_cols_pf(const P2Args a)
+// single spectrum; T column staged, K^ column staged when KSTAGE (else read
+// directly at the product)
+template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE>
+__global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(P::T) p2_cols_pf(const P2Args a)
         cp_async_commit();
     };
     auto prefetch_k = [&](int c) {
+        if constexpr (!KSTAGE) return;
         if (c >= a.ncols) return;
         const float* src = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
         for (int q = threadIdx.x; q < (int)((a.ldK * KW) >> 2); q += T) cp_async16(kst + 4 * q, src + 4 * q);
@@ -444,18 +446,23 @@ __global__ void __launch_bounds__(P::T) p2_cols_pf(const P2Args a)
         prefetch_t(c + gridDim.x);
         FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
             if (act) {
+                const float* kg = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
 #pragma unroll
                 for (int m = 0; m < RL; ++m) {
                     if constexpr (KREAL) {
-                        const float k = kst[j + m * NBL];
+                        const float k = KSTAGE ? kst[j + m * NBL] : __ldg(kg + j + m * NBL);
                         fz[m] = make_float2(fz[m].x * k, fz[m].y * k);
                     } else {
-                        fz[m] = cmul(fz[m], reinterpret_cast<const float2*>(kst)[j + m * NBL]);
+                        const float2 k = KSTAGE ? reinterpret_cast<const float2*>(kst)[j + m * NBL]
+                                                : __ldg(reinterpret_cast<const float2*>(kg) + j + m * NBL);
+                        fz[m] = cmul(fz[m], k);
                     }
                 }
             }
-            __syncthreads();  // K^ staging consumed
-            prefetch_k(c + gridDim.x);
+            if constexpr (KSTAGE) {
+                __syncthreads();  // K^ staging consumed
+                prefetch_k(c + gridDim.x);
+            }
             float2* Uc = a.U + (long long)c * a.ldU;
             InvChain::run(fz, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
                 if (act2) {
@@ -478,8 +485,8 @@ __global__ void __launch_bounds__(P::T) p2_cols_pf(const P2Args a)
     });
 }
 
-template <class P, int N, int UPB>
-__global__ void __launch_bounds__(P::T) p3_rows_pf(const P3Args a)
+template <class P, int N, int UPB, int MINB>
+__global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;

@@ -34,6 +34,7 @@ EXPORTS = (
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
     "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
+    "lp_serve_start", "lp_serve_submit", "lp_serve_poll", "lp_serve_stats", "lp_serve_stop",
 )
 
 
@@ -78,6 +79,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_set_pass_timing": ([_vp, _i], _i),
         "lp_map_noalloc": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp], _i),
         "lp_map_noalloc_scratch_bytes": ([], _sz),
+        "lp_serve_start": ([_vp, _i], _i),
+        "lp_serve_submit": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i,
+                             ctypes.POINTER(ctypes.c_uint64)], _i),
+        "lp_serve_poll": ([_vp, ctypes.c_uint64, _i, ctypes.POINTER(ctypes.c_double)], _i),
+        "lp_serve_stats": ([_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                            ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+        "lp_serve_stop": ([_vp], _i),
         "lp_get_pass_timing": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
@@ -278,3 +286,46 @@ def lp_map_noalloc(ctx: int, L, spectra: Sequence[int], out: Sequence, mode: int
 
 def lp_map_noalloc_scratch_bytes() -> int:
     return load_library().lp_map_noalloc_scratch_bytes()
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+def lp_serve_start(ctx: int, n_slots: int = 4) -> None:
+    _check(load_library().lp_serve_start(ctx, n_slots), "lp_serve_start")
+
+
+def lp_serve_submit(ctx: int, L, spectra: Sequence[int], out: Sequence,
+                    mode: int = LP_OUT_SAME) -> int:
+    """Queue one map request (device tensors, as lp_map); returns its ticket.
+    Keep L, the spectra and out alive until the ticket is polled."""
+    h, w = L.shape
+    ldo = out[0].stride(0)
+    t = ctypes.c_uint64()
+    _check(load_library().lp_serve_submit(ctx, L.data_ptr(), h, w, L.stride(0), _ptr_array(spectra),
+                                          len(spectra), _ptr_array([o.data_ptr() for o in out]),
+                                          ldo, mode, ctypes.byref(t)), "lp_serve_submit")
+    return t.value
+
+
+def lp_serve_poll(ctx: int, ticket: int, timeout_ms: int = -1):
+    """Latency in ms when finished, None on timeout; raises on failure."""
+    lat = ctypes.c_double()
+    st = load_library().lp_serve_poll(ctx, ticket, timeout_ms, ctypes.byref(lat))
+    if st == LP_ERR_TIMEOUT:
+        return None
+    _check(st, "lp_serve_poll")
+    return lat.value
+
+
+def lp_serve_stats(ctx: int) -> dict:
+    c, f = ctypes.c_uint64(), ctypes.c_uint64()
+    q, r = _i(), _i()
+    _check(load_library().lp_serve_stats(ctx, ctypes.byref(c), ctypes.byref(f), ctypes.byref(q),
+                                         ctypes.byref(r)), "lp_serve_stats")
+    return dict(completed=c.value, failed=f.value, queued=q.value, running=r.value)
+
+
+def lp_serve_stop(ctx: int) -> None:
+    _check(load_library().lp_serve_stop(ctx), "lp_serve_stop")

@@ -1,0 +1,234 @@
+"""Autotuner of the FFT plans (radix order and launch shape) per length.
+
+For each length N it builds small variant libraries that contain only N,
+each with one candidate radix sequence and one setting of the launch knobs
+of the prefetching kernels (work units per block, minimum resident blocks per
+SM, spectrum-column staging), times the three passes of a map whose padded
+size is N x N on the GPU, and keeps, for the fastest radix sequence, the best
+knob setting of each pass.  The result is written to ``tuned_plans.json``
+beside this file; ``build.py`` uses it for every length it lists.
+
+    python -m paper_1907_02891_gb300.tune --sizes 4704 8820 [--quick]
+
+Needs nvcc and one GPU.  Each variant is timed in a fresh subprocess (the
+variant libraries export the same symbols).
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import itertools
+import json
+import os
+import subprocess
+import sys
+import time
+from typing import Dict, List, Tuple
+
+from . import build as B
+
+TUNE_DIR = os.path.join(B.OUT, "tune")
+TUNED_JSON = os.path.join(B.HERE, "tuned_plans.json")
+COMMON_SRCS = ("api.cu", "spectrum.cu", "noalloc.cu", "serve.cpp")
+
+
+def candidate_plans(n: int, limit: int = 3) -> List[Tuple[int, ...]]:
+    """Radix sequences ordered like build.choose_plan, then the other orders
+    of the same multisets (first radix odd / large first)."""
+    scored = []
+    for f in B.factorizations(n):
+        if B.threads_for(n, f) > B.MAX_THREADS:
+            continue
+        scored.append(((len(f), max(f), -min(f)), f))
+    scored.sort()
+    out: List[Tuple[int, ...]] = []
+    for _, f in scored:
+        for perm in (tuple(sorted(f, reverse=True)), tuple(sorted(f))):
+            if perm not in out:
+                out.append(perm)
+        if len(out) >= limit:
+            break
+    return out[:limit]
+
+
+def _compile_common(jobs: int) -> List[str]:
+    os.makedirs(os.path.join(TUNE_DIR, "common"), exist_ok=True)
+    deps = max(os.path.getmtime(h) for h in B._headers())
+    srcs = [os.path.join(B.CSRC, f) for f in COMMON_SRCS]
+    objs = []
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        objs = list(ex.map(lambda s: B._compile(s, deps), srcs))
+    return objs
+
+
+def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
+    key = json.dumps([n, plan], sort_keys=True)
+    vid = hashlib.sha1(key.encode()).hexdigest()[:12]
+    d = os.path.join(TUNE_DIR, vid)
+    lib = os.path.join(d, "liblp.so")
+    if os.path.exists(lib):
+        return lib
+    os.makedirs(d, exist_ok=True)
+    r = list(plan["radices"])
+    text = B._SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=plan["f1"], f3=plan["f3"], ns=len(r),
+                             upb1=plan["upb"][0], upb2=plan["upb"][1], upb3=plan["upb"][2],
+                             minb1=plan["minb"][0], minb2=plan["minb"][1], minb3=plan["minb"][2],
+                             kstage="true" if plan["kstage"] else "false",
+                             rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
+    src = os.path.join(d, f"size_{n}.cu")
+    with open(src, "w") as fh:
+        fh.write(text)
+    reg = os.path.join(d, "registry.cu")
+    with open(reg, "w") as fh:
+        fh.write(B._REGISTRY_TU.format(decls=f"extern const SizeKernels kSize_{n};",
+                                       ptrs=f"&kSize_{n}", count=1))
+    objs = []
+    for s in (src, reg):
+        o = s[:-3] + ".o"
+        cmd = ["nvcc", *B.ARCH, *B.NVCC_FLAGS, "-I", B.CSRC, "-I", os.path.join(B.ROOT, "include"),
+               "-c", s, "-o", o]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed for variant {vid}:\n{res.stderr}")
+        objs.append(o)
+    res = subprocess.run(["nvcc", *B.ARCH, "-shared", "-o", lib, *common, *objs, "-lcudart"],
+                         capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"link failed for variant {vid}:\n{res.stderr}")
+    return lib
+
+
+_RUNNER = r"""
+import json, sys, time
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+import paper_1907_02891_gb300.lp as lp
+lp.load_library({lib!r})
+n, reps = {n}, {reps}
+hk = min(541, max(3, (n // 8) | 1))
+h = w = n - hk + 1
+dev = torch.device("cuda", 0)
+ctx = lp.lp_create(0)
+g = np.random.default_rng(1)
+L = torch.from_numpy(g.random((h, w), dtype=np.float32)).to(dev)
+r = np.hypot(*np.meshgrid(np.arange(hk) - hk // 2, np.arange(hk) - hk // 2, indexing="ij"))
+K = torch.from_numpy((r * r + 0.1) ** -1.25).to(dev)
+s = lp.lp_kernel_spectrum(ctx, K, pad_ny=n, pad_nx=n)
+out = torch.empty_like(L)
+flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+for _ in range(5):
+    lp.lp_map(ctx, L, [s], [out])
+lp.lp_sync_status(ctx)
+lp.lp_set_pass_timing(ctx, True)
+lp.lp_get_pass_timing(ctx)
+for _ in range(reps):
+    flush.zero_()
+    lp.lp_map(ctx, L, [s], [out])
+lp.lp_sync_status(ctx)
+t = lp.lp_get_pass_timing(ctx)
+print(json.dumps({{k: v[0] / max(1, v[1]) for k, v in t.items()}}))
+lp.lp_destroy(ctx)
+"""
+
+
+def time_variant(lib: str, n: int, reps: int) -> Dict[str, float]:
+    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        raise RuntimeError(f"timing failed for {lib}:\n{res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
+    base = B.plan_table_entry(n)
+    plans = candidate_plans(n, 2 if quick else 3)
+    knobs = []
+    for upb, minb, kst in itertools.product((1, 2), (1, 2, 3), (False, True)):
+        if quick and (minb == 3 and upb == 1):
+            continue
+        knobs.append((upb, minb, kst))
+    variants = []
+    for r in plans:
+        for upb, minb, kst in knobs:
+            p = dict(base)
+            p.update(radices=list(r), threads=B.threads_for(n, r), upb=[upb] * 3, minb=[minb] * 3,
+                     kstage=kst)
+            variants.append(p)
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        libs = list(ex.map(lambda p: _variant_lib(n, p, common), variants))
+    log(f"N={n}: built {len(libs)} variants in {time.time() - t0:.0f} s")
+    results = []
+    for p, lib in zip(variants, libs):
+        try:
+            t = time_variant(lib, n, 200 if n <= 5000 else 40)
+        except Exception as e:  # a variant that does not launch (resources) is skipped
+            log(f"  skip {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={p['kstage']}: "
+                f"{str(e).splitlines()[-1][:120]}")
+            continue
+        results.append((p, t))
+        log(f"  {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
+            + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+    if not results:
+        raise RuntimeError(f"no variant of {n} ran")
+    # per radix plan: best knob per pass; then the plan with the best total
+    best = None
+    for r in plans:
+        rs = [(p, t) for p, t in results if tuple(p["radices"]) == tuple(r)]
+        if not rs:
+            continue
+        choice, total = {}, 0.0
+        for k, name in enumerate(("p1_rows", "p2_cols", "p3_rows")):
+            p, t = min(rs, key=lambda x: x[1][name])
+            choice[name] = p
+            total += t[name]
+        if best is None or total < best[0]:
+            best = (total, r, choice)
+    total, r, choice = best
+    out = dict(base)
+    out.update(radices=list(r), threads=B.threads_for(n, r),
+               upb=[choice["p1_rows"]["upb"][0], choice["p2_cols"]["upb"][1], choice["p3_rows"]["upb"][2]],
+               minb=[choice["p1_rows"]["minb"][0], choice["p2_cols"]["minb"][1], choice["p3_rows"]["minb"][2]],
+               kstage=choice["p2_cols"]["kstage"], tuned_total_us=total * 1e3)
+    log(f"N={n}: chose {out['radices']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
+        f"(sum of best passes {total * 1e3:.1f} us)")
+    return out
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sizes", type=int, nargs="+", required=True)
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--jobs", type=int, default=0)
+    ap.add_argument("--out", default=TUNED_JSON)
+    ap.add_argument("--log", default=None)
+    args = ap.parse_args()
+    jobs = args.jobs or (os.cpu_count() or 1)
+    logf = open(args.log, "a") if args.log else None
+
+    def log(msg):
+        print(msg, flush=True)
+        if logf:
+            logf.write(msg + "\n")
+            logf.flush()
+
+    for n in args.sizes:
+        if n not in B.SIZES:
+            raise SystemExit(f"{n} is not in the supported size list")
+    common = _compile_common(jobs)
+    table = {}
+    if os.path.exists(args.out):
+        with open(args.out) as fh:
+            table = json.load(fh)
+    for n in args.sizes:
+        table[str(n)] = tune_size(n, args.quick, jobs, common, log)
+        with open(args.out, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+    log(f"wrote {args.out}")
+
+
+if __name__ == "__main__":
+    main()

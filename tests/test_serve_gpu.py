@@ -1,0 +1,133 @@
+"""Serving (continuous batching) through the C ABI.
+
+Each result must be the same alone (lp_map, one request at a time) and in
+the mix (many requests in flight on several streams); the kernels are
+deterministic, so the comparison is exact.  One request is also checked
+against the FP64 oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_02891_gb300 import lp  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _bank(ctx, sides, n_psf=4, psf_side=31):
+    Ks = [synth.psf_power_exp(psf_side, 0.742, 0.1, p, lam)
+          for (p, lam) in [(1.25, 40.0), (2.0, 80.0), (1.25, 120.0), (2.0, 200.0)][:n_psf]]
+    spectra = {}
+    for s in sides:
+        for i, K in enumerate(Ks):
+            spectra[(s, i)] = lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(DEV), max_h=s, max_w=s)
+    return Ks, spectra
+
+
+def _requests(n, sides, seed):
+    g = np.random.default_rng(seed)
+    reqs = []
+    for r in range(n):
+        s = int(sides[g.integers(0, len(sides))])
+        k = int(g.integers(1, 5))
+        ks = [int(x) for x in g.choice(4, size=k, replace=False)]
+        L = torch.from_numpy(synth.radiance_map(s, s, 6, seed * 100 + r, lit_fraction=0.02)).to(DEV)
+        reqs.append((s, ks, L))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix():
+    sides = (64, 160, 256, 512)
+    ctx = lp.lp_create(0)
+    try:
+        Ks, spectra = _bank(ctx, sides)
+        reqs = _requests(40, sides, 3)
+        alone = []
+        for s, ks, L in reqs:
+            outs = [torch.empty((s, s), device=DEV) for _ in ks]
+            lp.lp_map(ctx, L, [spectra[(s, i)] for i in ks], outs)
+            lp.lp_sync_status(ctx)
+            alone.append(outs)
+        lp.lp_serve_start(ctx, 4)
+        mixed, tickets = [], []
+        for s, ks, L in reqs:
+            outs = [torch.full((s, s), float("nan"), device=DEV) for _ in ks]
+            tickets.append(lp.lp_serve_submit(ctx, L, [spectra[(s, i)] for i in ks], outs))
+            mixed.append(outs)
+        lats = [lp.lp_serve_poll(ctx, t, timeout_ms=60000) for t in tickets]
+        assert all(x is not None and x > 0 for x in lats)
+        st = lp.lp_serve_stats(ctx)
+        assert st["completed"] == len(reqs) and st["failed"] == 0 and st["queued"] == 0
+        lp.lp_serve_stop(ctx)
+        for a, b in zip(alone, mixed):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        # one request against the oracle
+        s, ks, L = reqs[0]
+        Lh = L.cpu().numpy()
+        ref = oracle.conv_same(Lh, Ks[ks[0]])
+        got = mixed[0][0].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-5
+    finally:
+        lp.lp_destroy(ctx)
+
+
+def test_admission_waits_for_memory_and_refuses_oversize():
+    # budget: spectra + room for about one 512^2 request's workspace
+    ctx = lp.lp_create(0, 64 << 20)
+    try:
+        Ks, spectra = _bank(ctx, (512,), n_psf=2)
+        reqs = [(512, [0, 1], torch.from_numpy(synth.radiance_map(512, 512, 6, r)).to(DEV))
+                for r in range(6)]
+        lp.lp_serve_start(ctx, 4)
+        tickets, outs_all = [], []
+        for s, ks, L in reqs:
+            outs = [torch.empty((s, s), device=DEV) for _ in ks]
+            tickets.append(lp.lp_serve_submit(ctx, L, [spectra[(s, i)] for i in ks], outs))
+            outs_all.append(outs)
+        for t in tickets:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+        assert lp.lp_serve_stats(ctx)["failed"] == 0
+        # a request whose workspace exceeds the whole serving capacity
+        big = torch.zeros((8192, 8192), device=DEV)
+        Kb = torch.from_numpy(synth.psf_power_exp(31, 0.742, 0.1, 1.25, 40.0)).to(DEV)
+        with pytest.raises(lp.LpError) as e:
+            sb = lp.lp_kernel_spectrum(ctx, Kb, max_h=8192, max_w=8192)
+        assert e.value.status == lp.LP_ERR_OOM
+        lp.lp_serve_stop(ctx)
+    finally:
+        lp.lp_destroy(ctx)
+
+
+def test_serving_errors_and_bounded_poll():
+    ctx = lp.lp_create(0)
+    try:
+        Ks, spectra = _bank(ctx, (2048,), n_psf=1)
+        L = torch.from_numpy(synth.radiance_map(2048, 2048, 40, 5)).to(DEV)
+        out = torch.empty_like(L)
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_submit(ctx, L, [spectra[(2048, 0)]], [out])
+        assert e.value.status == lp.LP_ERR_BUSY
+        lp.lp_serve_start(ctx, 2)
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_start(ctx, 2)
+        assert e.value.status == lp.LP_ERR_BUSY
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_poll(ctx, 12345, 0)
+        assert e.value.status == lp.LP_ERR_INVALID
+        outs = [torch.empty_like(L) for _ in range(8)]
+        ts = [lp.lp_serve_submit(ctx, L, [spectra[(2048, 0)]], [o]) for o in outs]
+        assert lp.lp_serve_poll(ctx, ts[-1], timeout_ms=0) is None      # still running
+        for t in ts:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=-1) is not None
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        lp.lp_serve_stop(ctx)
+    finally:
+        lp.lp_destroy(ctx)
