@@ -75,6 +75,24 @@ def pass_bytes(H, W, ny, nx, n, s_k):
     }
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (the
+    bench's timing rule: the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(px_per_rank_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank maps its own map (weak scaling), so
+    the job outputs world x the per-rank pixels in the slowest rank's time."""
+    return px_per_rank_per_step * steps * world / (max_ms / 1e3) / 1e6
+
+
 def kernel_source_sha():
     h = hashlib.sha1()
     for p in KERNEL_SOURCES:
@@ -189,7 +207,7 @@ def run_reference(args, rank, world):
     import synth
     if rank != 0:
         return
-    wl = synth.WORKLOADS[args.workload]
+    wl = load_workload(args.workload)
     L = wl.radiance()
     Ks = wl.psfs()
     K = Ks[0]
@@ -223,6 +241,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+class _PaperShape:
+    """The paper's own map shape (Sec. 3) with its two PSFs."""
+    def __init__(self):
+        import synth
+        p = synth.PAPER_SHAPE
+        self.name, self.H, self.W, self.px_km = p["name"], p["H"], p["W"], p["px_km"]
+        self.seed = p["seed"]
+        self.psf_side = p["alr_side"]
+        self.psf_params = ("alr", "zsb")
+        self._p = p
+
+    def radiance(self):
+        import synth
+        return synth.paper_shape_inputs()[0]
+
+    def psfs(self):
+        import synth
+        p = self._p
+        return [synth.psf_alr(p["alr_side"], p["px_km"]),
+                synth.psf_power_exp(p["zsb_side"], p["px_km"], 0.1, 1.25, 26.0)]
+
+
+def load_workload(name):
+    import synth
+    if name == synth.PAPER_SHAPE["name"]:
+        return _PaperShape()
+    return synth.WORKLOADS[name]
+
+
 def workload_config(wl, pad):
     c = {"workload": wl.name, "map": f"{wl.H}x{wl.W}", "psf": f"{wl.psf_side}x{wl.psf_side}",
          "n_psf": len(wl.psf_params), "pixel_km": wl.px_km,
@@ -247,17 +294,21 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as td
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = synth.WORKLOADS[args.workload]
+    wl = load_workload(args.workload)
     H, W = wl.H, wl.W
     L_host = wl.radiance()
     Ks = wl.psfs()
     n = len(Ks)
+    hk_max = max(K.shape[0] for K in Ks)
 
     ctx = lp.lp_create(local_rank)
     stream = torch.cuda.current_stream()
     L = torch.from_numpy(L_host).to(dev)
     t0 = time.perf_counter()
-    specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), max_h=H, max_w=W)
+    # one padded size for all PSFs: the largest PSF's N_L + N_K - 1, rounded up
+    ny = lp.lp_supported_size(H + hk_max - 1)
+    nx = lp.lp_supported_size(W + hk_max - 1)
+    specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), pad_ny=ny, pad_nx=nx)
              for K in Ks]
     torch.cuda.synchronize()
     s0_ms = 1e3 * (time.perf_counter() - t0) / n
@@ -297,12 +348,8 @@ def run_ours(args, rank, world, local_rank):
     dev_ms = float(sum(step_ms))
     passes = lp.lp_get_pass_timing(ctx)
     lp.lp_set_pass_timing(ctx, False)
-    if dist:
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    px = float(H) * W * n * args.steps * world
-    value = px / (dev_ms / 1e3) / 1e6
+    dev_ms = max_over_ranks(dev_ms, dev)
+    value = whole_job_mpix_s(float(H) * W * n, args.steps, world, dev_ms)
 
     # roofline of the dominant pass
     model = pass_bytes(H, W, ny, nx, n, s_k)
@@ -332,12 +379,8 @@ def run_ours(args, rank, world, local_rank):
             lp.lp_map_host(ctx, Lh, specs, oh)
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": float(H) * W * n * args.e2e_steps * world / (e_ms / 1e3) / 1e6,
+        e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": whole_job_mpix_s(float(H) * W * n, args.e2e_steps, world, e_ms),
                "unit": UNIT, "h2d_bytes_per_step": 4 * H * W,
                "d2h_bytes_per_step": 4 * H * W * n, "steps": args.e2e_steps,
                "host_memory": "pinned"}
@@ -467,13 +510,21 @@ def run_serve(args, rank, world, local_rank):
     lp.lp_serve_stop(ctx)
     px = sum(q.side * q.side * len(q.kernels) for q in reqs)
     lat_ms = np.array(lat, dtype=np.float64)
+    by_side = {}
+    for s in sides:
+        sel = np.array([q.side == s for q in reqs])
+        if sel.any():
+            by_side[str(s)] = {"n": int(sel.sum()), "p50_ms": float(np.percentile(lat_ms[sel], 50)),
+                               "p99_ms": float(np.percentile(lat_ms[sel], 99)),
+                               "max_ms": float(lat_ms[sel].max())}
     line = {
         "metric": "serve p50/p99 ms", "value": float(np.percentile(lat_ms, 50)),
         "p99_ms": float(np.percentile(lat_ms, 99)), "unit": "ms", "higher_is_better": False,
         "n_gpus": 1, "requests": len(reqs), "slots": args.slots, "offered_load": args.load,
         "arrival_rate_hz": rate, "served_mpix_s": px / makespan / 1e6,
         "back_to_back_mpix_s": seq_mpix, "mean_service_ms": 1e3 * mean_service,
-        "makespan_s": makespan, "dtype": "f32", "data": "synthetic",
+        "makespan_s": makespan, "max_ms": float(lat_ms.max()), "by_side": by_side,
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve_tiles256-8192_bank8_psf201", "tile_sides": list(sides),
                    "psf": "201x201", "kernels_per_request": "1-8", "arrivals": "Poisson"},
         "clocks": clk,

@@ -45,7 +45,8 @@ SMEM_LIMIT = 227 * 1024
 SIZES = (
     45, 64, 96, 100, 120, 128, 160, 192, 210, 240, 256, 288, 320, 360, 384, 420, 480, 512,
     560, 640, 720, 768, 840, 960, 1024, 1120, 1260, 1344, 1536, 1680, 1792, 2048, 2250, 2520,
-    2688, 3072, 3360, 3584, 4096, 4320, 4704, 5040, 5376, 6144, 6720, 7168, 8192, 8400, 8820,
+    2688, 3072, 3360, 3584, 4096, 4320, 4704, 4800, 4860, 5040, 5120, 5376, 6144, 6720, 7168,
+    8192, 8400, 8640, 8820, 9000, 9216,
     10080, 10752, 12288, 13440, 15360, 16384, 17280,
 )
 
@@ -117,7 +118,7 @@ def plan_table_entry(n: int) -> dict:
             f = cand
             break
     return dict(radices=list(r), threads=t, f1=f, f3=f, smem=smem,
-                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True)
+                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True, tt=0)
 
 
 def plan_table() -> Dict[int, dict]:
@@ -133,7 +134,10 @@ def plan_table() -> Dict[int, dict]:
         t = tuned.get(str(n))
         if t:
             e.update(radices=list(t["radices"]), threads=threads_for(n, t["radices"]),
-                     upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]))
+                     upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
+                     tt=int(t.get("tt", 0)))
+            if e["tt"]:
+                e["threads"] = e["tt"]
         table[n] = e
     return table
 
@@ -145,7 +149,7 @@ _SIZE_TU = """// generated by paper_1907_02891_gb300/build.py -- one supported F
 namespace lpk {{
 namespace {{
 constexpr int kN = {n};
-using P = Plan<kN, Seq<{seq}>>;
+using P = Plan<kN, Seq<{seq}>, {tt}>;   // threads per transform (0 = one butterfly each)
 constexpr int kF1 = {f1}, kF3 = {f3};
 constexpr int kSmem = P::SMEM_BYTES;
 constexpr int kSmem2 = P::SMEM_BYTES + 8 * kN;   // + a parked column (batched / multi-class)
@@ -284,6 +288,7 @@ def generate() -> List[str]:
     for n, p in table.items():
         r = list(p["radices"])
         text = _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=p["f1"], f3=p["f3"], ns=len(r),
+                               tt=p.get("tt", 0),
                                upb1=p["upb"][0], upb2=p["upb"][1], upb3=p["upb"][2],
                                minb1=p["minb"][0], minb2=p["minb"][1], minb3=p["minb"][2],
                                kstage="true" if p["kstage"] else "false",

@@ -73,24 +73,146 @@ struct P3Args {
     TwChain tw;  // reversed chain of the row plan
 };
 
-template <int N, class FwdSeq>
+template <int N, class FwdSeq, int TT_ = 0>
 struct Plan {
     using Fwd = FwdSeq;
     using Inv = Reverse<FwdSeq>;
     static_assert(SeqInfo<Fwd>::product == N, "radices must multiply to N");
     static constexpr int R0 = SeqInfo<Fwd>::first;   // first forward radix
     static constexpr int RL = SeqInfo<Fwd>::last;    // last forward radix
-    static constexpr int T = ((N / SeqInfo<Fwd>::min_r) + 31) / 32 * 32;  // threads per FFT
+    // threads per transform: one butterfly per thread in every stage by
+    // default (N / smallest radix, rounded up to whole warps); fewer threads
+    // own several butterflies in the stages with more butterflies
+    static constexpr int T = TT_ > 0 ? TT_ : ((N / SeqInfo<Fwd>::min_r) + 31) / 32 * 32;
     // shared memory (complex elements) of one transform: the larger padded
-    // extent of the forward and the reversed chain
-    // (rounded up to an even count so that staging areas placed after it
-    // start on a 16-byte boundary, as cp.async of 16 bytes requires)
+    // extent of the forward and the reversed chain, rounded up to an even
+    // count so that staging areas placed after it start on a 16-byte
+    // boundary (as cp.async of 16 bytes requires)
     static constexpr int SMEM_ELEMS = ((ChainExtent<Fwd>::value > ChainExtent<Inv>::value
                                             ? ChainExtent<Fwd>::value
                                             : ChainExtent<Inv>::value) + 1) / 2 * 2;
     static constexpr int SMEM_BYTES = 8 * SMEM_ELEMS;
     static_assert(T <= 1024, "too many threads per transform");
+    using FwdChain = Chain<N, -1, 1, 0, T, Fwd>;
+    using InvChain = Chain<N, +1, 1, 0, T, Inv>;
+    static constexpr int E0 = FwdChain::E;                    // forward first stage
+    static constexpr int EL = Chain<N, -1, N / RL, 0, T, Seq<RL>>::E;  // forward last stage
+    static constexpr int EI = InvChain::E;                    // inverse first stage (= EL)
+    static constexpr int EJ = Chain<N, +1, N / R0, 0, T, Seq<R0>>::E;  // inverse last stage
 };
+
+// P2's spectrum product on the forward column's last-stage outputs (thread
+// t, butterfly j = t + e T holds frequencies j + m N/RL).
+template <class P, int N, bool KREAL, bool STAGED>
+__device__ __forceinline__ void spectrum_product(float2 (&f)[P::EL][P::RL], int t, const void* kcol,
+                                                 const float* kst)
+{
+    constexpr int RL = P::RL, NBL = N / RL;
+#pragma unroll
+    for (int e = 0; e < P::EL; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NBL) continue;
+#pragma unroll
+        for (int m = 0; m < RL; ++m) {
+            const int u = j + m * NBL;
+            if constexpr (KREAL) {
+                const float k = STAGED ? kst[u] : __ldg(static_cast<const float*>(kcol) + u);
+                f[e][m] = make_float2(f[e][m].x * k, f[e][m].y * k);
+            } else {
+                const float2 k = STAGED ? reinterpret_cast<const float2*>(kst)[u]
+                                        : __ldg(static_cast<const float2*>(kcol) + u);
+                f[e][m] = cmul(f[e][m], k);
+            }
+        }
+    }
+}
+
+// P2's inverse-output store: rows of the crop window of column Uc.
+template <class P, int N>
+__device__ __forceinline__ void store_column(const float2 (&o)[P::EJ][P::R0], int t, float2* Uc,
+                                             int r0, int Hout, int HoutPad)
+{
+    constexpr int R0 = P::R0, NB0 = N / R0;
+#pragma unroll
+    for (int e = 0; e < P::EJ; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NB0) continue;
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            int rr = j + m * NB0 - r0;
+            if (rr < 0) rr += N;
+            if (rr < Hout) Uc[rr] = o[e][m];
+        }
+    }
+    if (HoutPad != Hout && t == 0) Uc[Hout] = make_float2(0.f, 0.f);
+}
+
+// P1's split of the packed transform Z (in shared memory, natural order)
+// into the half spectra of rows a and b: {2 X_a[c], 2 X_b[c]} -> T[c][pair].
+template <int N, int T>
+__device__ __forceinline__ void unpack_rows(const float2* sm, int t, int ncols, float4* Tq, long long ldq,
+                                            int pair)
+{
+    for (int c = t; c < ncols; c += T) {
+        const int cm = (c == 0) ? 0 : N - c;
+        const float2 zc = sm[c], zm = sm[cm];
+        float4 o;
+        o.x = zc.x + zm.x;       // 2 X_a = Z[c] + conj Z[N-c]
+        o.y = zc.y - zm.y;
+        o.z = zc.y + zm.y;       // 2 X_b = -i (Z[c] - conj Z[N-c])
+        o.w = -(zc.x - zm.x);
+        Tq[(long long)c * ldq + pair] = o;
+    }
+}
+
+// P1/P3 hand the last stage's outputs to shared memory in natural order.
+template <class P, int N, int E, int R>
+__device__ __forceinline__ void to_smem_natural(const float2 (&z)[E][R], int t, float2* sm)
+{
+    constexpr int NBL = N / R;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NBL) continue;
+#pragma unroll
+        for (int m = 0; m < R; ++m) sm[j + m * NBL] = z[e][m];
+    }
+    __syncthreads();
+}
+
+// P3's first-stage input: Z[k] = A[k] + i B[k] from the stored half spectra
+// q = {A, B} of k (k <= N/2) or of N-k (Hermitian extension).
+__device__ __forceinline__ float2 packed_inverse_input(float4 q, bool lo, bool vb)
+{
+    if (!vb) {
+        q.z = 0.f;
+        q.w = 0.f;
+    }
+    return lo ? make_float2(q.x - q.w, q.y + q.z) : make_float2(q.x + q.w, q.z - q.y);
+}
+
+// P3's final store: real part -> row a, imaginary part -> row b, crop columns.
+template <class P, int N>
+__device__ __forceinline__ void store_rows(const float2 (&o)[P::EJ][P::R0], int t, float* oa, float* ob,
+                                           bool vb, int c0, int Wout)
+{
+    constexpr int RJ = P::R0, NBJ = N / RJ;
+#pragma unroll
+    for (int e = 0; e < P::EJ; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NBJ) continue;
+#pragma unroll
+        for (int m = 0; m < RJ; ++m) {
+            int cc = j + m * NBJ - c0;
+            if (cc < 0) cc += N;
+            if (cc < Wout) {
+                oa[cc] = o[e][m].x;
+                if (vb) ob[cc] = o[e][m].y;
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // P1: row R2C of two packed rows per transform, F transforms per block.
@@ -101,7 +223,6 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
-    constexpr int RL = P::RL, NBL = N / RL;
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
     float2* sm = smem2 + f * P::SMEM_ELEMS;
@@ -111,81 +232,28 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
     const float* La = a.L + (long long)ra * a.ldl;
     const float* Lb = a.L + (long long)rb * a.ldl;
 
-    float2 v[R0];
-    if (t < NB0) {
+    float2 v[P::E0][R0];
+#pragma unroll
+    for (int e = 0; e < P::E0; ++e) {
+        const int j = t + e * T;
+        if (j >= NB0) continue;
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
-            const int col = t + m * NB0;
+            const int col = j + m * NB0;
             const bool in = col < a.W;
-            v[m].x = (in && va) ? __ldg(La + col) : 0.f;
-            v[m].y = (in && vb) ? __ldg(Lb + col) : 0.f;
+            v[e][m].x = (in && va) ? __ldg(La + col) : 0.f;
+            v[e][m].y = (in && vb) ? __ldg(Lb + col) : 0.f;
         }
     }
-    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-    FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[RL], int j, bool act) {
-        __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int m = 0; m < RL; ++m) sm[j + m * NBL] = z[m];
-        }
-        __syncthreads();
-        if (pair < a.npairs) {
-            float4* Tq = reinterpret_cast<float4*>(a.T);
-            for (int c = t; c < a.ncols; c += T) {
-                const int cm = (c == 0) ? 0 : N - c;
-                const float2 zc = sm[c], zm = sm[cm];
-                const float zr = zc.x, zi = zc.y;
-                const float wr = zm.x, wi = -zm.y;
-                // 2 X_a = Z[c] + conj Z[N-c] ; 2 X_b = -i (Z[c] - conj Z[N-c])
-                float4 o;
-                o.x = zr + wr;
-                o.y = zi + wi;
-                o.z = zi - wi;
-                o.w = -(zr - wr);
-                Tq[((long long)c * a.ldT) / 2 + pair] = o;
-            }
-        }
+    P::FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[P::EL][P::RL], int tt) {
+        to_smem_natural<P, N>(z, tt, sm);
+        if (pair < a.npairs) unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
     });
 }
 
 // ---------------------------------------------------------------------------
 // P2: per column forward FFT, spectrum product, inverse FFT, row crop.
 // ---------------------------------------------------------------------------
-template <class P, int N, bool KREAL>
-__device__ __forceinline__ void p2_product_inverse(const P2Args& a, int c, int s, float2 (&g)[P::RL],
-                                                   int j, bool act, float2* sm)
-{
-    constexpr int R0 = P::R0, NB0 = N / R0;
-    constexpr int RL = P::RL, NBL = N / RL;
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
-    if (act) {
-        if constexpr (KREAL) {
-            const float* kc = static_cast<const float*>(a.K[s]) + (long long)c * a.ldK + j;
-#pragma unroll
-            for (int m = 0; m < RL; ++m) {
-                const float k = __ldg(kc + m * NBL);
-                g[m] = make_float2(g[m].x * k, g[m].y * k);
-            }
-        } else {
-            const float2* kc = static_cast<const float2*>(a.K[s]) + (long long)c * a.ldK + j;
-#pragma unroll
-            for (int m = 0; m < RL; ++m) g[m] = cmul(g[m], __ldg(kc + m * NBL));
-        }
-    }
-    float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
-    InvChain::run(g, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
-        if (act2) {
-#pragma unroll
-            for (int m = 0; m < R0; ++m) {
-                int rr = j2 + m * NB0 - a.r0;
-                if (rr < 0) rr += N;
-                if (rr < a.Hout) Uc[rr] = o[m];
-            }
-        }
-        if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
-    });
-}
-
 // One spectrum of the batched column pass: the forward column is parked in
 // shared memory F (natural order); product with spectrum s, inverse, store.
 // Not inlined: as a loop body it would let the compiler keep the whole
@@ -194,14 +262,22 @@ template <class P, int N, bool KREAL>
 __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, const float2* F, float2* sm)
 {
     constexpr int RL = P::RL, NBL = N / RL;
-    const int j = threadIdx.x;
-    const bool act = j < NBL;
-    float2 g[RL];
-    if (act) {
+    const int t = threadIdx.x;
+    float2 g[P::EL][RL];
 #pragma unroll
-        for (int m = 0; m < RL; ++m) g[m] = F[j + m * NBL];
+    for (int e = 0; e < P::EL; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NBL) continue;
+#pragma unroll
+        for (int m = 0; m < RL; ++m) g[e][m] = F[j + m * NBL];
     }
-    p2_product_inverse<P, N, KREAL>(a, c, s, g, j, act, sm);
+    const long long kw = KREAL ? 1 : 2;
+    spectrum_product<P, N, KREAL, false>(g, t, static_cast<const float*>(a.K[s]) + (long long)c * a.ldK * kw,
+                                         nullptr);
+    float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
+    P::InvChain::run(g, t, sm, a.twi, [&](float2(&o)[P::EJ][P::R0], int tt) {
+        store_column<P, N>(o, tt, Uc, a.r0, a.Hout, a.HoutPad);
+    });
 }
 
 template <class P, int N, bool KREAL, bool MULTI>
@@ -215,25 +291,36 @@ __global__ void __launch_bounds__(P::T) p2_cols(const __grid_constant__ P2Args a
     const int t = threadIdx.x;
     const float2* col = a.T + (long long)c * a.ldT;
 
-    float2 v[R0];
-    if (t < NB0) {
+    float2 v[P::E0][R0];
+#pragma unroll
+    for (int e = 0; e < P::E0; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NB0) continue;
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
-            const int row = t + m * NB0;
-            v[m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
+            const int row = j + m * NB0;
+            v[e][m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
         }
     }
-    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-    FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
+    P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
         if constexpr (MULTI) {
             float2* F = smem2 + P::SMEM_ELEMS;  // parked forward column
-            if (act) {
 #pragma unroll
-                for (int m = 0; m < RL; ++m) F[j + m * NBL] = fz[m];
+            for (int e = 0; e < P::EL; ++e) {
+                const int j = tt + e * P::T;
+                if (j >= NBL) continue;
+#pragma unroll
+                for (int m = 0; m < RL; ++m) F[j + m * NBL] = fz[e][m];
             }
             for (int s = 0; s < a.nspec; ++s) p2_spectrum_pass<P, N, KREAL>(a, c, s, F, sm);
         } else {
-            p2_product_inverse<P, N, KREAL>(a, c, 0, fz, j, act, sm);
+            const long long kw = KREAL ? 1 : 2;
+            spectrum_product<P, N, KREAL, false>(fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * kw,
+                                                 nullptr);
+            float2* Uc = a.U + (long long)c * a.ldU;
+            P::InvChain::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
+                store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
+            });
         }
     });
 }
@@ -247,8 +334,7 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
-    constexpr int RI = SeqInfo<typename P::Inv>::first, NBI = N / RI;
-    constexpr int RJ = SeqInfo<typename P::Inv>::last, NBJ = N / RJ;
+    constexpr int RI = P::RL, NBI = N / RI;
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
     float2* sm = smem2 + f * P::SMEM_ELEMS;
@@ -260,40 +346,27 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
     const bool live = pair < a.npairs;
     const bool vb = rb < a.Hout;
 
-    float2 v[RI];
-    if (t < NBI) {
+    float2 v[P::EI][RI];
+#pragma unroll
+    for (int e = 0; e < P::EI; ++e) {
+        const int j = t + e * T;
+        if (j >= NBI) continue;
 #pragma unroll
         for (int m = 0; m < RI; ++m) {
-            const int k = t + m * NBI;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int k = j + m * NBI;
             const bool lo = k < a.ncols;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
             if (live) q = __ldg(Uq + (long long)(lo ? k : N - k) * ldq + pair);
-            if (!vb) {
-                q.z = 0.f;
-                q.w = 0.f;
-            }
-            // Z[k] = A[k] + i B[k]; for k > Nx/2, A[k] = conj A[N-k], same for B
-            v[m] = lo ? make_float2(q.x - q.w, q.y + q.z) : make_float2(q.x + q.w, q.z - q.y);
+            v[e][m] = packed_inverse_input(q, lo, vb);
         }
     }
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
-    InvChain::run(v, t, sm, a.tw, [&](float2(&o)[RJ], int j, bool act) {
-        if (act && live) {
+    P::InvChain::run(v, t, sm, a.tw, [&](float2(&o)[P::EJ][P::R0], int tt) {
+        if (live) {
             float* oa = a.out[sidx] + (long long)ra * a.ldo;
-            float* ob = oa + a.ldo;
-#pragma unroll
-            for (int m = 0; m < RJ; ++m) {
-                int cc = j + m * NBJ - a.c0;
-                if (cc < 0) cc += N;
-                if (cc < a.Wout) {
-                    oa[cc] = o[m].x;
-                    if (vb) ob[cc] = o[m].y;
-                }
-            }
+            store_rows<P, N>(o, tt, oa, oa + a.ldo, vb, a.c0, a.Wout);
         }
     });
 }
-
 
 // ---------------------------------------------------------------------------
 // Prefetching variants.  Each block handles UPB work units (u, u + gridDim.x,
@@ -301,7 +374,8 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
 // into a shared-memory staging area with cp.async (16-byte pieces where
 // aligned), so global-memory latency overlaps the butterflies instead of
 // stalling them.  cp.async.wait_group is a hardware wait: no spin loop is
-// involved.
+// involved.  Units are unrolled at compile time: a loop back-edge makes the
+// compiler keep about 70 more registers live per thread.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
@@ -316,8 +390,7 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-
-// staging bytes of the persistent kernels (host and device agree on these)
+// staging bytes of the prefetching kernels (host and device agree on these)
 __host__ __device__ constexpr long long p1_stage_bytes(int Wst) { return 8ll * Wst; }
 __host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long ldK, bool kreal, bool kstage)
 {
@@ -325,16 +398,12 @@ __host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long 
 }
 __host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll * ncols; }
 
-// Units per block of the prefetching kernels: the block handles units
-// blockIdx.x + i * gridDim.x for i < UPB, unrolled at compile time (a loop
-// back-edge makes the compiler keep ~70 more registers live per thread).
 template <class P, int N, int UPB, int MINB>
 __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
-    constexpr int RL = P::RL, NBL = N / RL;
     float2* sm = smem2;
     float* st = reinterpret_cast<float*>(smem2 + P::SMEM_ELEMS);  // rows a, b: 2 x Wst floats
     const int Wst = a.Wst;
@@ -360,37 +429,24 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
         __syncthreads();
         const int t = threadIdx.x;
         const bool vb = 2 * pair + 1 < a.H;
-        float2 v[R0];
-        if (t < NB0) {
+        float2 v[P::E0][R0];
+#pragma unroll
+        for (int e = 0; e < P::E0; ++e) {
+            const int j = t + e * T;
+            if (j >= NB0) continue;
 #pragma unroll
             for (int m = 0; m < R0; ++m) {
-                const int col = t + m * NB0;
+                const int col = j + m * NB0;
                 const bool in = col < a.W;
-                v[m].x = in ? st[col] : 0.f;
-                v[m].y = (in && vb) ? st[Wst + col] : 0.f;
+                v[e][m].x = in ? st[col] : 0.f;
+                v[e][m].y = (in && vb) ? st[Wst + col] : 0.f;
             }
         }
         __syncthreads();  // staging consumed
         prefetch(pair + gridDim.x);
-        using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-        FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[RL], int j, bool act) {
-            __syncthreads();
-            if (act) {
-#pragma unroll
-                for (int m = 0; m < RL; ++m) sm[j + m * NBL] = z[m];
-            }
-            __syncthreads();
-            float4* Tq = reinterpret_cast<float4*>(a.T);
-            for (int c = t; c < a.ncols; c += T) {
-                const int cm = (c == 0) ? 0 : N - c;
-                const float2 zc = sm[c], zm = sm[cm];
-                float4 o;  // {2 X_a[c], 2 X_b[c]}
-                o.x = zc.x + zm.x;
-                o.y = zc.y - zm.y;
-                o.z = zc.y + zm.y;
-                o.w = -(zc.x - zm.x);
-                Tq[((long long)c * a.ldT) / 2 + pair] = o;
-            }
+        P::FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[P::EL][P::RL], int tt) {
+            to_smem_natural<P, N>(z, tt, sm);
+            unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
         });
     };
     prefetch(blockIdx.x);
@@ -408,7 +464,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
-    constexpr int RL = P::RL, NBL = N / RL;
+    constexpr int RL = P::RL;
     constexpr int KW = KREAL ? 1 : 2;                    // floats per K^ element
     float2* sm = smem2;
     float2* tst = smem2 + P::SMEM_ELEMS;                 // ldT complex
@@ -427,53 +483,34 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
         for (int q = threadIdx.x; q < (int)((a.ldK * KW) >> 2); q += T) cp_async16(kst + 4 * q, src + 4 * q);
         cp_async_commit();
     };
-    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
 
     auto unit = [&](int c) {
         cp_async_wait_all();
         __syncthreads();
         const int t = threadIdx.x;
-        float2 v[R0];
-        if (t < NB0) {
+        float2 v[P::E0][R0];
+#pragma unroll
+        for (int e = 0; e < P::E0; ++e) {
+            const int j = t + e * T;
+            if (j >= NB0) continue;
 #pragma unroll
             for (int m = 0; m < R0; ++m) {
-                const int row = t + m * NB0;
-                v[m] = row < a.H ? tst[row] : make_float2(0.f, 0.f);
+                const int row = j + m * NB0;
+                v[e][m] = row < a.H ? tst[row] : make_float2(0.f, 0.f);
             }
         }
         __syncthreads();
         prefetch_t(c + gridDim.x);
-        FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
-            if (act) {
-                const float* kg = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
-#pragma unroll
-                for (int m = 0; m < RL; ++m) {
-                    if constexpr (KREAL) {
-                        const float k = KSTAGE ? kst[j + m * NBL] : __ldg(kg + j + m * NBL);
-                        fz[m] = make_float2(fz[m].x * k, fz[m].y * k);
-                    } else {
-                        const float2 k = KSTAGE ? reinterpret_cast<const float2*>(kst)[j + m * NBL]
-                                                : __ldg(reinterpret_cast<const float2*>(kg) + j + m * NBL);
-                        fz[m] = cmul(fz[m], k);
-                    }
-                }
-            }
+        P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
+            spectrum_product<P, N, KREAL, KSTAGE>(
+                fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW, kst);
             if constexpr (KSTAGE) {
                 __syncthreads();  // K^ staging consumed
                 prefetch_k(c + gridDim.x);
             }
             float2* Uc = a.U + (long long)c * a.ldU;
-            InvChain::run(fz, j, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
-                if (act2) {
-#pragma unroll
-                    for (int m = 0; m < R0; ++m) {
-                        int rr = j2 + m * NB0 - a.r0;
-                        if (rr < 0) rr += N;
-                        if (rr < a.Hout) Uc[rr] = o[m];
-                    }
-                }
-                if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+            P::InvChain::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
+                store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
             });
         });
     };
@@ -490,8 +527,7 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
-    constexpr int RI = SeqInfo<typename P::Inv>::first, NBI = N / RI;
-    constexpr int RJ = SeqInfo<typename P::Inv>::last, NBJ = N / RJ;
+    constexpr int RI = P::RL, NBI = N / RI;
     float2* sm = smem2;
     float4* ust = reinterpret_cast<float4*>(smem2 + P::SMEM_ELEMS);  // ncols x {A, B}
     const int sidx = blockIdx.y;
@@ -503,7 +539,6 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
         for (int k = threadIdx.x; k < a.ncols; k += T) cp_async16(ust + k, Uq + (long long)k * ldq + pair);
         cp_async_commit();
     };
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
 
     auto unit = [&](int pair) {
         cp_async_wait_all();
@@ -511,36 +546,23 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
         const int t = threadIdx.x;
         const int ra = 2 * pair, rb = ra + 1;
         const bool vb = rb < a.Hout;
-        float2 v[RI];
-        if (t < NBI) {
+        float2 v[P::EI][RI];
+#pragma unroll
+        for (int e = 0; e < P::EI; ++e) {
+            const int j = t + e * T;
+            if (j >= NBI) continue;
 #pragma unroll
             for (int m = 0; m < RI; ++m) {
-                const int k = t + m * NBI;
+                const int k = j + m * NBI;
                 const bool lo = k < a.ncols;
-                float4 q = ust[lo ? k : N - k];
-                if (!vb) {
-                    q.z = 0.f;
-                    q.w = 0.f;
-                }
-                v[m] = lo ? make_float2(q.x - q.w, q.y + q.z) : make_float2(q.x + q.w, q.z - q.y);
+                v[e][m] = packed_inverse_input(ust[lo ? k : N - k], lo, vb);
             }
         }
         __syncthreads();
         prefetch(pair + gridDim.x);
-        InvChain::run(v, t, sm, a.tw, [&](float2(&o)[RJ], int j, bool act) {
-            if (act) {
-                float* oa = a.out[sidx] + (long long)ra * a.ldo;
-                float* ob = oa + a.ldo;
-#pragma unroll
-                for (int m = 0; m < RJ; ++m) {
-                    int cc = j + m * NBJ - a.c0;
-                    if (cc < 0) cc += N;
-                    if (cc < a.Wout) {
-                        oa[cc] = o[m].x;
-                        if (vb) ob[cc] = o[m].y;
-                    }
-                }
-            }
+        P::InvChain::run(v, t, sm, a.tw, [&](float2(&o)[P::EJ][P::R0], int tt) {
+            float* oa = a.out[sidx] + (long long)ra * a.ldo;
+            store_rows<P, N>(o, tt, oa, oa + a.ldo, vb, a.c0, a.Wout);
         });
     };
     prefetch(blockIdx.x);
@@ -553,7 +575,7 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 // ---------------------------------------------------------------------------
 // P2 for Sec. 2.2 Eq. (4): several source classes, one PSF each.  The
 // forward column transform of each class's T is multiplied by its spectrum
-// and accumulated in registers; one inverse transform follows.
+// and accumulated; one inverse transform follows.
 // ---------------------------------------------------------------------------
 struct P2MArgs {
     const float2* T[kMaxSpectraPerLaunch];
@@ -577,35 +599,31 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
 {
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
-    using FwdChain = Chain<N, -1, 1, 0, typename P::Fwd>;
     const int t = threadIdx.x;
     const float2* col = a.T[q] + (long long)c * a.ldT;
-    float2 v[R0];
-    if (t < NB0) {
+    float2 v[P::E0][R0];
+#pragma unroll
+    for (int e = 0; e < P::E0; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NB0) continue;
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
-            const int row = t + m * NB0;
-            v[m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
+            const int row = j + m * NB0;
+            v[e][m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
         }
     }
-    FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[RL], int j, bool act) {
-        if (act) {
-            if constexpr (KREAL) {
-                const float* kc = static_cast<const float*>(a.K[q]) + (long long)c * a.ldK + j;
+    P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
+        const long long kw = KREAL ? 1 : 2;
+        spectrum_product<P, N, KREAL, false>(fz, tt, static_cast<const float*>(a.K[q]) + (long long)c * a.ldK * kw,
+                                             nullptr);
 #pragma unroll
-                for (int m = 0; m < RL; ++m) {
-                    const float k = __ldg(kc + m * NBL);
-                    float2& acc = ACC[j + m * NBL];
-                    acc.x += fz[m].x * k;
-                    acc.y += fz[m].y * k;
-                }
-            } else {
-                const float2* kc = static_cast<const float2*>(a.K[q]) + (long long)c * a.ldK + j;
+        for (int e = 0; e < P::EL; ++e) {
+            const int j = tt + e * P::T;
+            if (j >= NBL) continue;
 #pragma unroll
-                for (int m = 0; m < RL; ++m) {
-                    float2& acc = ACC[j + m * NBL];
-                    acc = cadd(acc, cmul(fz[m], __ldg(kc + m * NBL)));
-                }
+            for (int m = 0; m < RL; ++m) {
+                float2& acc = ACC[j + m * NBL];
+                acc = cadd(acc, fz[e][m]);
             }
         }
     });
@@ -615,36 +633,29 @@ template <class P, int N, bool KREAL>
 __global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2MArgs a)
 {
     extern __shared__ float2 smem2[];
-    constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
     float2* sm = smem2;
     float2* ACC = smem2 + P::SMEM_ELEMS;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
-    using InvChain = Chain<N, +1, 1, 0, typename P::Inv>;
 
     for (int i = t; i < N; i += blockDim.x) ACC[i] = make_float2(0.f, 0.f);
     // every element of ACC is owned by one thread (j + m N/RL), so the
-    // accumulation needs no barrier; the chain's own barriers order sm
+    // accumulation needs no barrier; the chain's own barriers order sm and
+    // the initialisation above
     for (int q = 0; q < a.nclass; ++q) p2_class_pass<P, N, KREAL>(a, c, q, ACC, sm);
     __syncthreads();
-    float2 acc[RL];
-    const bool act = t < NBL;
-    if (act) {
+    float2 acc[P::EL][RL];
 #pragma unroll
-        for (int m = 0; m < RL; ++m) acc[m] = ACC[t + m * NBL];
+    for (int e = 0; e < P::EL; ++e) {
+        const int j = t + e * P::T;
+        if (j >= NBL) continue;
+#pragma unroll
+        for (int m = 0; m < RL; ++m) acc[e][m] = ACC[j + m * NBL];
     }
     float2* Uc = a.U + (long long)c * a.ldU;
-    InvChain::run(acc, t, sm, a.twi, [&](float2(&o)[R0], int j2, bool act2) {
-        if (act2) {
-#pragma unroll
-            for (int m = 0; m < R0; ++m) {
-                int rr = j2 + m * NB0 - a.r0;
-                if (rr < 0) rr += N;
-                if (rr < a.Hout) Uc[rr] = o[m];
-            }
-        }
-        if (a.HoutPad != a.Hout && j2 == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+    P::InvChain::run(acc, t, sm, a.twi, [&](float2(&o)[P::EJ][P::R0], int tt) {
+        store_column<P, N>(o, tt, Uc, a.r0, a.Hout, a.HoutPad);
     });
 }
 

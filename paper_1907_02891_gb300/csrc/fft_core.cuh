@@ -331,43 +331,50 @@ template <int... Rs> struct ChainExtent<Seq<Rs...>> {
 };
 
 // ---------------------------------------------------------------------------
-// Stage chain in FP32.  `run` takes the inputs of the first stage in v
-// (thread t holds x[t + m N/R] when t < N/R), runs every stage, exchanging
+// Stage chain in FP32.  TT threads cooperate on one transform; in a stage
+// with NB = N/R butterflies, thread t owns butterflies j = t + e TT for
+// e < E = ceil(NB / TT) (j < NB).  `run` takes the inputs of the first
+// stage in v[e] (thread t holds x[j + m N/R]), runs every stage, exchanging
 // through shared memory `sm` between stages, and hands the last stage's
-// outputs (thread t holds y[t + m N/R_last]) to `fin(v, t, active)`.
+// outputs (v[e] holds y[j + m N/R_last]) to `fin(v, t)`.
 // Every thread of the block must call it (it contains barriers).
 // ---------------------------------------------------------------------------
-template <int N, int DIR, int Ns, int SIdx, class S> struct Chain;
+template <int N, int DIR, int Ns, int SIdx, int TT, class S> struct Chain;
 
-template <int N, int DIR, int Ns, int SIdx, int R, int... Rest>
-struct Chain<N, DIR, Ns, SIdx, Seq<R, Rest...>> {
+template <int N, int DIR, int Ns, int SIdx, int TT, int R, int... Rest>
+struct Chain<N, DIR, Ns, SIdx, TT, Seq<R, Rest...>> {
     static constexpr int NB = N / R;
+    static constexpr int E = (NB + TT - 1) / TT;
 
     template <class Fin>
-    __device__ __forceinline__ static void run(float2 (&v)[R], int t, float2* sm,
+    __device__ __forceinline__ static void run(float2 (&v)[E][R], int t, float2* sm,
                                                const TwChain& tw, Fin&& fin)
     {
-        const bool act = t < NB;
-        if (act) {
-            if constexpr (Ns > 1) {
-                const float2* tab = tw.p[SIdx];
-                // opaque to the optimiser: keeps the table loads inside loops
-                // that repeat a chain (n spectra, n classes) instead of hoisting
-                // every stage's twiddles into registers across iterations
-                asm volatile("" : "+l"(tab));
-                tab += t % Ns;
 #pragma unroll
-                for (int m = 1; m < R; ++m) {
-                    float2 w = __ldg(tab + (m - 1) * Ns);
-                    if constexpr (DIR > 0) w.y = -w.y;
-                    v[m] = cmul(v[m], w);
+        for (int e = 0; e < E; ++e) {
+            const int j = t + e * TT;
+            if (j < NB) {
+                if constexpr (Ns > 1) {
+                    const float2* tab = tw.p[SIdx];
+                    // opaque to the optimiser: keeps the table loads inside
+                    // loops that repeat a chain instead of hoisting every
+                    // stage's twiddles into registers across iterations
+                    asm volatile("" : "+l"(tab));
+                    tab += j % Ns;
+#pragma unroll
+                    for (int m = 1; m < R; ++m) {
+                        float2 w = __ldg(tab + (m - 1) * Ns);
+                        if constexpr (DIR > 0) w.y = -w.y;
+                        v[e][m] = cmul(v[e][m], w);
+                    }
                 }
+                Dft<R, DIR, float2>::run(v[e]);
             }
-            Dft<R, DIR, float2>::run(v);
         }
         if constexpr (sizeof...(Rest) == 0) {
-            fin(v, t, act);
+            fin(v, t);
         } else {
+            using Next = Chain<N, DIR, Ns * R, SIdx + 1, TT, Seq<Rest...>>;
             constexpr int R2 = SeqInfo<Seq<Rest...>>::first;
             constexpr int NB2 = N / R2;
             constexpr int P = Ns * R;
@@ -375,19 +382,27 @@ struct Chain<N, DIR, Ns, SIdx, Seq<R, Rest...>> {
             static_assert(NB2 % P == 0, "reader stride must be a multiple of the group size");
             constexpr int rstride = NB2 + q * (NB2 / P);
             __syncthreads();  // earlier readers of sm are done
-            if (act) {
-                float2* w0 = sm + (t / Ns) * (P + q) + (t % Ns);
 #pragma unroll
-                for (int m = 0; m < R; ++m) w0[m * Ns] = v[m];
+            for (int e = 0; e < E; ++e) {
+                const int j = t + e * TT;
+                if (j < NB) {
+                    float2* w0 = sm + (j / Ns) * (P + q) + (j % Ns);
+#pragma unroll
+                    for (int m = 0; m < R; ++m) w0[m * Ns] = v[e][m];
+                }
             }
             __syncthreads();
-            float2 w[R2];
-            if (t < NB2) {
-                const float2* r0 = sm + t + q * (t / P);
+            float2 w[Next::E][R2];
 #pragma unroll
-                for (int m = 0; m < R2; ++m) w[m] = r0[m * rstride];
+            for (int e = 0; e < Next::E; ++e) {
+                const int j = t + e * TT;
+                if (j < NB2) {
+                    const float2* r0 = sm + j + q * (j / P);
+#pragma unroll
+                    for (int m = 0; m < R2; ++m) w[e][m] = r0[m * rstride];
+                }
             }
-            Chain<N, DIR, Ns * R, SIdx + 1, Seq<Rest...>>::run(w, t, sm, tw, fin);
+            Next::run(w, t, sm, tw, fin);
         }
     }
 };

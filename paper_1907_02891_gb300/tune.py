@@ -73,6 +73,7 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
     os.makedirs(d, exist_ok=True)
     r = list(plan["radices"])
     text = B._SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=plan["f1"], f3=plan["f3"], ns=len(r),
+                             tt=plan.get("tt", 0),
                              upb1=plan["upb"][0], upb2=plan["upb"][1], upb3=plan["upb"][2],
                              minb1=plan["minb"][0], minb2=plan["minb"][1], minb3=plan["minb"][2],
                              kstage="true" if plan["kstage"] else "false",
@@ -152,11 +153,20 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
         knobs.append((upb, minb, kst))
     variants = []
     for r in plans:
-        for upb, minb, kst in knobs:
-            p = dict(base)
-            p.update(radices=list(r), threads=B.threads_for(n, r), upb=[upb] * 3, minb=[minb] * 3,
-                     kstage=kst)
-            variants.append(p)
+        # threads per transform: one butterfly per thread in every stage (0),
+        # or as many as the stage with the fewest butterflies (whole warps)
+        tts = [0]
+        few = (n // max(r) + 31) // 32 * 32
+        if few < B.threads_for(n, r):
+            tts.append(few)
+        for tt in tts:
+            for upb, minb, kst in knobs:
+                if tt and kst:          # staging only varies at the default thread count
+                    continue
+                p = dict(base)
+                p.update(radices=list(r), threads=tt or B.threads_for(n, r), upb=[upb] * 3,
+                         minb=[minb] * 3, kstage=kst, tt=tt)
+                variants.append(p)
     t0 = time.time()
     with cf.ThreadPoolExecutor(jobs) as ex:
         libs = list(ex.map(lambda p: _variant_lib(n, p, common), variants))
@@ -170,14 +180,15 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
                 f"{str(e).splitlines()[-1][:120]}")
             continue
         results.append((p, t))
-        log(f"  {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
+        log(f"  {p['radices']} tt={p['tt']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
             + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
     if not results:
         raise RuntimeError(f"no variant of {n} ran")
-    # per radix plan: best knob per pass; then the plan with the best total
+    # per (radix plan, threads per transform): best knob per pass; then the
+    # combination with the best total
     best = None
-    for r in plans:
-        rs = [(p, t) for p, t in results if tuple(p["radices"]) == tuple(r)]
+    for r, tt in sorted({(tuple(p["radices"]), p["tt"]) for p, _ in results}):
+        rs = [(p, t) for p, t in results if tuple(p["radices"]) == r and p["tt"] == tt]
         if not rs:
             continue
         choice, total = {}, 0.0
@@ -186,14 +197,14 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
             choice[name] = p
             total += t[name]
         if best is None or total < best[0]:
-            best = (total, r, choice)
-    total, r, choice = best
+            best = (total, r, choice, tt)
+    total, r, choice, tt = best
     out = dict(base)
-    out.update(radices=list(r), threads=B.threads_for(n, r),
+    out.update(radices=list(r), threads=tt or B.threads_for(n, r), tt=tt,
                upb=[choice["p1_rows"]["upb"][0], choice["p2_cols"]["upb"][1], choice["p3_rows"]["upb"][2]],
                minb=[choice["p1_rows"]["minb"][0], choice["p2_cols"]["minb"][1], choice["p3_rows"]["minb"][2]],
                kstage=choice["p2_cols"]["kstage"], tuned_total_us=total * 1e3)
-    log(f"N={n}: chose {out['radices']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
+    log(f"N={n}: chose {out['radices']} tt={out['tt']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
         f"(sum of best passes {total * 1e3:.1f} us)")
     return out
 

@@ -165,6 +165,25 @@ WORKLOADS = {
                                 BASE_SEED + 3),
 }
 
+# The paper's own shape (Sec. 3): an 11920 x 11804 map of 404.4 m pixels and
+# two maps from it -- the all-sky light-pollution ratio PSF of Eq. (12)-(13)
+# out to 300 km (1485 x 1485 support) and a zenith-brightness stand-in out to
+# the 195 km reach used for the LPTRAN PSF (965 x 965 support; the LPTRAN
+# values are not available, a power-law-exponential PSF stands in).
+PAPER_SHAPE = dict(name="map11920x11804_alr1485_zsb965", H=11920, W=11804, px_km=0.4044,
+                   n_cities=3300, lit_fraction=0.05, seed=BASE_SEED + 5,
+                   alr_side=1485, zsb_side=965)
+
+
+def paper_shape_inputs():
+    """Radiance map and the two PSFs (ALR Eq. (12)-(13); ZSB stand-in)."""
+    p = PAPER_SHAPE
+    L = radiance_map(p["H"], p["W"], p["n_cities"], p["seed"], lit_fraction=p["lit_fraction"])
+    K_alr = psf_alr(p["alr_side"], p["px_km"])
+    K_zsb = psf_power_exp(p["zsb_side"], p["px_km"], 0.1, 1.25, 26.0)
+    return L, [K_alr, K_zsb]
+
+
 # Serving bank: 8 PSFs of side 201 (radius 100 px), lambda x p in {1.25, 2.0}
 SERVE_BANK_PARAMS = _family(0.1, (1.25, 2.0), (40.0, 80.0, 120.0, 200.0))
 SERVE_PSF_SIDE = 201

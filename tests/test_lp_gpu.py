@@ -236,6 +236,24 @@ def test_map16384_psf801_sampled(ctx):
     assert _sampled_check(L, K, B, wl.seed + 100) <= TOL_FP32
 
 
+def test_paper_shape_two_maps_one_forward_transform(ctx):
+    """Sec. 3: two maps (all-sky ratio, Eq. (12)-(13), 1485^2; zenith-brightness
+    stand-in, 965^2) of an 11920 x 11804 map at 404.4 m, from one call."""
+    L, Ks = synth.paper_shape_inputs()
+    H, W = L.shape
+    ny = lp.lp_supported_size(H + 1485 - 1)
+    nx = lp.lp_supported_size(W + 1485 - 1)
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), pad_ny=ny, pad_nx=nx) for K in Ks]
+    outs = [torch.empty((H, W), dtype=torch.float32, device=DEV) for _ in Ks]
+    lp.lp_map(ctx, dev(L), specs, outs)
+    lp.lp_sync_status(ctx)
+    for k, (K, o) in enumerate(zip(Ks, outs)):
+        assert _sampled_check(L, K, o.cpu().numpy(), synth.PAPER_SHAPE["seed"] + 10 + k,
+                              n=2048, top=32) <= TOL_FP32, k
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+
+
 # --- cache, budget, validation, bounded waits ---------------------------------
 
 def test_spectrum_cache_refcount(ctx):
