@@ -192,9 +192,9 @@ cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
     const long long sm = kSmem + p1_stage_bytes(a.Wst);
     if (sm <= kMaxSmem) {{
-        p1_rows_pf<P, kN, kUPB1, kMINB1><<<persistent_grid(a.npairs, kUPB1), P::T, sm, s>>>(a);
+        p1_rows_pf<P, kN, kUPB1, kMINB1><<<persistent_grid(a.npairs - a.pair0, kUPB1), P::T, sm, s>>>(a);
     }} else {{
-        p1_rows<P, kN, kF1><<<(a.npairs + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
+        p1_rows<P, kN, kF1><<<(a.npairs - a.pair0 + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
     }}
     return cudaGetLastError();
 }}
@@ -248,9 +248,9 @@ cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
     const long long sm = kSmem + p3_stage_bytes(a.ncols);
     if (sm <= kMaxSmem) {{
-        p3_rows_pf<P, kN, kUPB3, kMINB3><<<dim3(persistent_grid(a.npairs, kUPB3), nspec), P::T, sm, s>>>(a);
+        p3_rows_pf<P, kN, kUPB3, kMINB3><<<dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec), P::T, sm, s>>>(a);
     }} else {{
-        p3_rows<P, kN, kF3><<<dim3((a.npairs + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
+        p3_rows<P, kN, kF3><<<dim3((a.npairs - a.pair0 + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
     }}
     return cudaGetLastError();
 }}

@@ -282,6 +282,10 @@ extern "C" void lp_destroy(lp_ctx* ctx)
         cudaEventDestroy(pe.stop);
     }
     for (auto ev : ctx->tim_pool) cudaEventDestroy(ev);
+    for (auto ev : ctx->hs_events) cudaEventDestroy(ev);
+    if (ctx->hs_lfree) cudaEventDestroy(ctx->hs_lfree);
+    if (ctx->hs_in) cudaStreamDestroy(ctx->hs_in);
+    if (ctx->hs_out) cudaStreamDestroy(ctx->hs_out);
     delete ctx;
 }
 
@@ -537,6 +541,89 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     return LP_OK;
 }
 
+// The three passes as separate launches (row pairs [pair0, pair1) for the
+// row passes), composed by lp_launch_map and by the banded host-buffer map.
+static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float* L, int h, int w, int ldl,
+                                     const MapDims& d, float2* T, int pair0, int pair1, cudaStream_t st)
+{
+    P1Args a1;
+    a1.L = L;
+    a1.ldl = ldl;
+    a1.H = h;
+    a1.W = w;
+    a1.Wst = (w + 3) / 4 * 4;
+    a1.vec16 = ((reinterpret_cast<uintptr_t>(L) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
+    a1.T = T;
+    a1.ldT = d.ldT;
+    a1.pair0 = pair0;
+    a1.npairs = pair1;
+    a1.ncols = d.ncols;
+    a1.tw = px->fwd;
+    const int tok = lp_pass_begin(ctx, 0, st);
+    CUDA_TRY(px->k->p1(a1, st));
+    lp_pass_end(ctx, tok, st);
+    return LP_OK;
+}
+
+// column pass for spectra [base, base+cnt) into U (cnt blocks of ncols x ldU)
+static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectrum* const* spectra, int base,
+                                int cnt, int h, const MapDims& d, const float2* T, float2* U, cudaStream_t st)
+{
+    const lp_spectrum* s0 = spectra[0];
+    // the real-spectrum kernel needs every spectrum of the launch real:
+    // split the chunk by kind
+    int k0 = 0;
+    while (k0 < cnt) {
+        const int kind = spectra[base + k0]->is_real;
+        int k1 = k0;
+        while (k1 < cnt && spectra[base + k1]->is_real == kind) ++k1;
+        P2Args a2;
+        a2.T = T;
+        a2.ldT = d.ldT;
+        a2.H = h;
+        for (int i = 0; i < kMaxSpectraPerLaunch; ++i)
+            a2.K[i] = (i < k1 - k0) ? spectra[base + k0 + i]->data : nullptr;
+        a2.ldK = s0->ldK;
+        a2.nspec = k1 - k0;
+        a2.U = U + (size_t)k0 * d.ncols * d.ldU;
+        a2.ldU = d.ldU;
+        a2.specU = (long long)d.ncols * d.ldU;
+        a2.r0 = d.r0;
+        a2.Hout = d.Hout;
+        a2.HoutPad = (int)d.ldU;
+        a2.ncols = d.ncols;
+        a2.twf = py->fwd;
+        a2.twi = py->rev;
+        const int tok = lp_pass_begin(ctx, 1, st);
+        CUDA_TRY(py->k->p2(a2, kind != 0, st));
+        lp_pass_end(ctx, tok, st);
+        k0 = k1;
+    }
+    return LP_OK;
+}
+
+static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDims& d, const float2* U, int cnt,
+                                     float* const* out, int ldo, int pair0, int pair1, cudaStream_t st)
+{
+    P3Args a3;
+    a3.U = U;
+    a3.ldU = d.ldU;
+    a3.specU = (long long)d.ncols * d.ldU;
+    a3.Hout = d.Hout;
+    a3.pair0 = pair0;
+    a3.npairs = pair1;
+    for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i < cnt ? out[i] : nullptr;
+    a3.ldo = ldo;
+    a3.c0 = d.c0;
+    a3.Wout = d.Wout;
+    a3.ncols = d.ncols;
+    a3.tw = px->rev;
+    const int tok = lp_pass_begin(ctx, 2, st);
+    CUDA_TRY(px->k->p3(a3, cnt, st));
+    lp_pass_end(ctx, tok, st);
+    return LP_OK;
+}
+
 // Launch P1, P2, P3 for n spectra (the validated sequence of lp_map).
 lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
@@ -550,70 +637,12 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     if (ps != LP_OK) return ps;
     float2* T = static_cast<float2*>(ws);
     float2* U = T + (size_t)d.ncols * d.ldT;
-    const int npairs = (int)(d.ldT / 2);
-
-    P1Args a1;
-    a1.L = L;
-    a1.ldl = ldl;
-    a1.H = h;
-    a1.W = w;
-    a1.Wst = (w + 3) / 4 * 4;
-    a1.vec16 = ((reinterpret_cast<uintptr_t>(L) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
-    a1.T = T;
-    a1.ldT = d.ldT;
-    a1.npairs = npairs;
-    a1.ncols = d.ncols;
-    a1.tw = px->fwd;
-    int tok = lp_pass_begin(ctx, 0, st);
-    CUDA_TRY(px->k->p1(a1, st));
-    lp_pass_end(ctx, tok, st);
-
+    if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
-        // the real-spectrum kernel needs every spectrum of the launch real;
-        // split the chunk by kind
-        int k0 = 0;
-        while (k0 < cnt) {
-            const int kind = spectra[base + k0]->is_real;
-            int k1 = k0;
-            while (k1 < cnt && spectra[base + k1]->is_real == kind) ++k1;
-            P2Args a2;
-            a2.T = T;
-            a2.ldT = d.ldT;
-            a2.H = h;
-            for (int i = 0; i < kMaxSpectraPerLaunch; ++i)
-                a2.K[i] = (i < k1 - k0) ? spectra[base + k0 + i]->data : nullptr;
-            a2.ldK = s0->ldK;
-            a2.nspec = k1 - k0;
-            a2.U = U + (size_t)k0 * d.ncols * d.ldU;
-            a2.ldU = d.ldU;
-            a2.specU = (long long)d.ncols * d.ldU;
-            a2.r0 = d.r0;
-            a2.Hout = d.Hout;
-            a2.HoutPad = (int)d.ldU;
-            a2.ncols = d.ncols;
-            a2.twf = py->fwd;
-            a2.twi = py->rev;
-            tok = lp_pass_begin(ctx, 1, st);
-            CUDA_TRY(py->k->p2(a2, kind != 0, st));
-            lp_pass_end(ctx, tok, st);
-            k0 = k1;
-        }
-        P3Args a3;
-        a3.U = U;
-        a3.ldU = d.ldU;
-        a3.specU = (long long)d.ncols * d.ldU;
-        a3.Hout = d.Hout;
-        a3.npairs = (int)(d.ldU / 2);
-        for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i < cnt ? out[base + i] : nullptr;
-        a3.ldo = ldo;
-        a3.c0 = d.c0;
-        a3.Wout = d.Wout;
-        a3.ncols = d.ncols;
-        a3.tw = px->rev;
-        tok = lp_pass_begin(ctx, 2, st);
-        CUDA_TRY(px->k->p3(a3, cnt, st));
-        lp_pass_end(ctx, tok, st);
+        if ((ps = launch_columns(ctx, py, spectra, base, cnt, h, d, T, U, st)) != LP_OK) return ps;
+        if ((ps = launch_rows_inverse(ctx, px, d, U, cnt, out + base, ldo, 0, (int)(d.ldU / 2), st)) != LP_OK)
+            return ps;
     }
     return LP_OK;
 }
@@ -642,6 +671,28 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     return lp_launch_map(ctx, L, h, w, ldl, spectra, n, out, ldo, d, ws, s);
 }
 
+// Host-buffer map, pipelined in row bands: the map is copied up band by band
+// on an internal stream while the row pass transforms the bands already on
+// the device, and the output is copied down band by band while the inverse
+// row pass produces the next bands.  The column pass needs every row, so it
+// runs between the two.  Everything is ordered after the caller's stream at
+// entry, and the caller's stream waits for the last copy at exit.
+static constexpr int kHostBands = 8;
+
+static lp_status host_streams(lp_ctx* ctx)
+{
+    if (ctx->hs_in) return LP_OK;
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hs_in, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hs_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2 * kHostBands + 2; ++i) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->hs_events.push_back(e);
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->hs_lfree, cudaEventDisableTiming));
+    return LP_OK;
+}
+
 extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w, int ldl,
                                  const lp_spectrum* const* spectra, int n, float* const* out_host,
                                  int ldo, lp_outmode mode, lp_precision prec, void* stream)
@@ -654,10 +705,14 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const lp_spectrum* s0 = spectra[0];
+    const PlanRec *py, *px;
+    if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
+    if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
     // staging: L (h x w, packed) then n outputs (Hout x Wout, packed)
     const size_t lbytes = 4ull * (size_t)h * w;
     const size_t obytes = 4ull * (size_t)d.Hout * d.Wout;
     const size_t need = ((lbytes + 255) / 256 * 256) + (size_t)n * ((obytes + 255) / 256 * 256);
+    std::lock_guard<std::mutex> host_lock(ctx->host_mu);  // one host map in flight per context
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
         if (ctx->staging_bytes < need) {
@@ -672,8 +727,10 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
             if (st != LP_OK) return st;
             ctx->staging = p;
             ctx->staging_bytes = need;
+            ctx->hs_lfree_valid = false;
         }
     }
+    if ((st = host_streams(ctx)) != LP_OK) return st;
     char* base = static_cast<char*>(ctx->staging);
     float* dL = reinterpret_cast<float*>(base);
     std::vector<float*> dout(n);
@@ -682,15 +739,67 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
         dout[k] = reinterpret_cast<float*>(p);
         p += (obytes + 255) / 256 * 256;
     }
-    CUDA_TRY(cudaMemcpy2DAsync(dL, 4ull * w, L_host, 4ull * ldl, 4ull * w, h, cudaMemcpyHostToDevice, s));
     void* ws = nullptr;
     st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
-    st = lp_launch_map(ctx, dL, h, w, w, spectra, n, dout.data(), d.Wout, d, ws, s);
-    if (st != LP_OK) return st;
-    for (int k = 0; k < n; ++k)
-        CUDA_TRY(cudaMemcpy2DAsync(out_host[k], 4ull * ldo, dout[k], 4ull * d.Wout, 4ull * d.Wout, d.Hout,
-                                   cudaMemcpyDeviceToHost, s));
+    float2* T = static_cast<float2*>(ws);
+    float2* U = T + (size_t)d.ncols * d.ldT;
+    cudaEvent_t* ev = ctx->hs_events.data();
+    cudaEvent_t ev_start = ev[0], ev_end = ev[1];
+    cudaEvent_t* ev_in = ev + 2;                 // kHostBands
+    cudaEvent_t* ev_out = ev + 2 + kHostBands;   // kHostBands
+    cudaEvent_t ev_lfree = ctx->hs_lfree;
+
+    // The upload only has to wait until the previous host map's row pass has
+    // read the staging map (so it overlaps that map's column and inverse
+    // passes and its download); the passes and the download run after the
+    // caller's earlier work on its stream, which includes the previous host
+    // map's download.
+    CUDA_TRY(cudaEventRecord(ev_start, s));
+    if (ctx->hs_lfree_valid) CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_lfree, 0));
+    else CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_start, 0));
+    CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_start, 0));
+
+    const int npairs = (int)(d.ldT / 2);
+    const int nb_in = npairs < kHostBands ? npairs : kHostBands;
+    for (int b = 0; b < nb_in; ++b) {
+        const int q0 = (int)((long long)npairs * b / nb_in), q1 = (int)((long long)npairs * (b + 1) / nb_in);
+        const int r0 = 2 * q0, r1 = (2 * q1 < h) ? 2 * q1 : h;
+        if (r1 > r0)
+            CUDA_TRY(cudaMemcpy2DAsync(dL + (size_t)r0 * w, 4ull * w, L_host + (size_t)r0 * ldl, 4ull * ldl,
+                                       4ull * w, r1 - r0, cudaMemcpyHostToDevice, ctx->hs_in));
+        CUDA_TRY(cudaEventRecord(ev_in[b], ctx->hs_in));
+        CUDA_TRY(cudaStreamWaitEvent(s, ev_in[b], 0));
+        if ((st = launch_rows_forward(ctx, px, dL, h, w, w, d, T, q0, q1, s)) != LP_OK) return st;
+    }
+    CUDA_TRY(cudaEventRecord(ev_lfree, s));  // the staging map may be overwritten after this
+    ctx->hs_lfree_valid = true;
+    const int opairs = (int)(d.ldU / 2);
+    const int nb_out = opairs < kHostBands ? opairs : kHostBands;
+    for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {
+        const int cnt = (n - cb) < kMaxSpectraPerLaunch ? (n - cb) : kMaxSpectraPerLaunch;
+        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, s)) != LP_OK) return st;
+        for (int b = 0; b < nb_out; ++b) {
+            const int q0 = (int)((long long)opairs * b / nb_out), q1 = (int)((long long)opairs * (b + 1) / nb_out);
+            if ((st = launch_rows_inverse(ctx, px, d, U, cnt, dout.data() + cb, d.Wout, q0, q1, s)) != LP_OK)
+                return st;
+            CUDA_TRY(cudaEventRecord(ev_out[b], s));
+            CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_out[b], 0));
+            const int r0 = 2 * q0, r1 = (2 * q1 < d.Hout) ? 2 * q1 : d.Hout;
+            if (r1 <= r0) continue;
+            for (int k = cb; k < cb + cnt; ++k)
+                CUDA_TRY(cudaMemcpy2DAsync(out_host[k] + (size_t)r0 * ldo, 4ull * ldo, dout[k] + (size_t)r0 * d.Wout,
+                                           4ull * d.Wout, 4ull * d.Wout, r1 - r0, cudaMemcpyDeviceToHost,
+                                           ctx->hs_out));
+        }
+        if (cb + cnt < n) {
+            // the next chunk's inverse row pass overwrites U: wait for these copies
+            CUDA_TRY(cudaEventRecord(ev_end, ctx->hs_out));
+            CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(ev_end, ctx->hs_out));
+    CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
     return LP_OK;
 }
 
@@ -762,6 +871,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
         a1.vec16 = ((reinterpret_cast<uintptr_t>(L[t]) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
         a1.T = Tb + (size_t)t * d.ncols * d.ldT;
         a1.ldT = d.ldT;
+        a1.pair0 = 0;
         a1.npairs = npairs;
         a1.ncols = d.ncols;
         a1.tw = px->fwd;
@@ -805,6 +915,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a3.ldU = d.ldU;
     a3.specU = 0;
     a3.Hout = d.Hout;
+    a3.pair0 = 0;
     a3.npairs = (int)(d.ldU / 2);
     for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i == 0 ? out : nullptr;
     a3.ldo = ldo;

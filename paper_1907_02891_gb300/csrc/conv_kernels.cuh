@@ -38,6 +38,7 @@ struct P1Args {
     int vec16;  // rows can be copied in 16-byte pieces (aligned base, ldl % 4 == 0, W % 4 == 0)
     float2* T;
     long long ldT;
+    int pair0;   // first row pair of this launch (pairs pair0 .. npairs-1)
     int npairs;  // ceil(H/2)
     int ncols;   // Nx/2 + 1
     TwChain tw;  // forward chain of the row plan
@@ -65,6 +66,7 @@ struct P3Args {
     long long ldU;
     long long specU;
     int Hout, npairs;
+    int pair0;  // first output row pair of this launch
     float* out[kMaxSpectraPerLaunch];
     long long ldo;
     int c0;  // first kept column (mod Nx)
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
     float2* sm = smem2 + f * P::SMEM_ELEMS;
-    const int pair = blockIdx.x * F + f;
+    const int pair = a.pair0 + blockIdx.x * F + f;
     const int ra = 2 * pair, rb = ra + 1;
     const bool va = ra < a.H, vb = rb < a.H;
     const float* La = a.L + (long long)ra * a.ldl;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
     const int f = threadIdx.x / T;
     const int t = threadIdx.x - f * T;
     float2* sm = smem2 + f * P::SMEM_ELEMS;
-    const int pair = blockIdx.x * F + f;
+    const int pair = a.pair0 + blockIdx.x * F + f;
     const int sidx = blockIdx.y;
     const int ra = 2 * pair, rb = ra + 1;
     const float4* Uq = reinterpret_cast<const float4*>(a.U + (long long)sidx * a.specU);
@@ -449,9 +451,9 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
             unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
         });
     };
-    prefetch(blockIdx.x);
+    prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {
-        const int pair = blockIdx.x + decltype(I)::value * gridDim.x;
+        const int pair = a.pair0 + blockIdx.x + decltype(I)::value * gridDim.x;
         if (pair < a.npairs) unit(pair);
     });
 }
@@ -565,9 +567,9 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
             store_rows<P, N>(o, tt, oa, oa + a.ldo, vb, a.c0, a.Wout);
         });
     };
-    prefetch(blockIdx.x);
+    prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {
-        const int pair = blockIdx.x + decltype(I)::value * gridDim.x;
+        const int pair = a.pair0 + blockIdx.x + decltype(I)::value * gridDim.x;
         if (pair < a.npairs) unit(pair);
     });
 }

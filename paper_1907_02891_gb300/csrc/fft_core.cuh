@@ -159,14 +159,35 @@ __device__ __forceinline__ C rot(C a)
 // ---------------------------------------------------------------------------
 // In-register DFT of size R (unnormalised), natural order in and out.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+
+// Split of a composite radix r = a * b for the in-register DFT: coprime
+// factors when there are any (prime-factor algorithm, no internal
+// twiddles), the largest such a with a*a <= r; otherwise the largest
+// divisor a with a*a <= r (4 x r/4 for powers of two).  1 for primes.
 __host__ __device__ constexpr int small_factor(int r)
 {
-    // largest divisor a of r with 1 < a and a*a <= r; powers of two split 4 x r/4
+    int coprime = 1;
+    for (int a = 2; a < r; ++a)
+        if (r % a == 0 && gcd_i(a, r / a) == 1 && (coprime == 1 || a * a <= r)) coprime = a;
+    if (coprime > 1) {
+        // prefer the smaller of the two coprime factors first
+        const int b = r / coprime;
+        return coprime < b ? coprime : b;
+    }
     if (r % 4 == 0 && r > 4) return 4;
     int best = 1;
     for (int a = 2; a * a <= r; ++a)
         if (r % a == 0) best = a;
     return best;
+}
+
+// modular inverse of a mod m (a, m coprime), compile time
+__host__ __device__ constexpr int inv_mod(int a, int m)
+{
+    for (int x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return 1;
 }
 
 template <int R, int DIR, class C> struct Dft;
@@ -233,9 +254,15 @@ __device__ __forceinline__ void dft_odd_prime(C* v)
     sfor<0, P>([&](auto K_) { v[decltype(K_)::value] = y[decltype(K_)::value]; });
 }
 
-// Composite R = A * B (Cooley-Tukey in registers): n = B n1 + n2,
-// k = k1 + A k2.  A-point DFTs over n1, twiddle exp(DIR i 2pi n2 k1 / R),
-// B-point DFTs over n2.
+// Composite R = A * B.
+//  * gcd(A, B) = 1: prime-factor (Good-Thomas) algorithm.  With input index
+//    n = (B n1 + A n2) mod R and output index k = k1 B (B^-1 mod A) +
+//    k2 A (A^-1 mod B) mod R (k1 = k mod A, k2 = k mod B), the R-point DFT
+//    is A-point DFTs over n1 followed by B-point DFTs over n2 with no
+//    twiddles in between; both index maps are compile-time permutations.
+//  * otherwise Cooley-Tukey in registers: n = B n1 + n2, k = k1 + A k2;
+//    A-point DFTs over n1, twiddle exp(DIR i 2pi n2 k1 / R), B-point DFTs
+//    over n2.
 template <int R, int DIR, class C> struct Dft {
     static constexpr int A = small_factor(R);
     static constexpr int B = R / A;
@@ -244,6 +271,30 @@ template <int R, int DIR, class C> struct Dft {
         if constexpr (A == 1) {
             static_assert(R % 2 == 1, "prime radix must be odd here");
             dft_odd_prime<R, DIR, C>(v);
+        } else if constexpr (gcd_i(A, B) == 1) {
+            constexpr int EA = B * inv_mod(B % A, A);  // k -> k1 component of the CRT
+            constexpr int EB = A * inv_mod(A % B, B);
+            C t[R];
+            sfor<0, B>([&](auto N2_) {
+                constexpr int n2 = decltype(N2_)::value;
+                C a[A];
+                sfor<0, A>([&](auto N1_) {
+                    constexpr int n1 = decltype(N1_)::value;
+                    a[n1] = v[(B * n1 + A * n2) % R];
+                });
+                Dft<A, DIR, C>::run(a);
+                sfor<0, A>([&](auto K1_) { t[n2 * A + decltype(K1_)::value] = a[decltype(K1_)::value]; });
+            });
+            sfor<0, A>([&](auto K1_) {
+                constexpr int k1 = decltype(K1_)::value;
+                C b[B];
+                sfor<0, B>([&](auto N2_) { b[decltype(N2_)::value] = t[decltype(N2_)::value * A + k1]; });
+                Dft<B, DIR, C>::run(b);
+                sfor<0, B>([&](auto K2_) {
+                    constexpr int k2 = decltype(K2_)::value;
+                    v[(k1 * EA + k2 * EB) % R] = b[k2];
+                });
+            });
         } else {
             C t[R];
             sfor<0, B>([&](auto N2_) {

@@ -75,6 +75,12 @@ struct lp_ctx {
     bool timing = false;
     std::vector<PassEvent> tim_pending;
     std::vector<cudaEvent_t> tim_pool;
+    // pipelined host-buffer map
+    std::mutex host_mu;
+    cudaStream_t hs_in = nullptr, hs_out = nullptr;
+    std::vector<cudaEvent_t> hs_events;
+    cudaEvent_t hs_lfree = nullptr;  // previous host map's row pass done with the staging map
+    bool hs_lfree_valid = false;
 };
 
 lp_status lp_fail(lp_status st, const char* fmt, ...);

@@ -108,9 +108,9 @@ import torch
 sys.path.insert(0, {root!r})
 import paper_1907_02891_gb300.lp as lp
 lp.load_library({lib!r})
-n, reps = {n}, {reps}
+n, reps, side = {n}, {reps}, {side}
 hk = min(541, max(3, (n // 8) | 1))
-h = w = n - hk + 1
+h = w = side if side > 0 else n - hk + 1
 dev = torch.device("cuda", 0)
 ctx = lp.lp_create(0)
 g = np.random.default_rng(1)
@@ -135,15 +135,15 @@ lp.lp_destroy(ctx)
 """
 
 
-def time_variant(lib: str, n: int, reps: int) -> Dict[str, float]:
-    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps)
+def time_variant(lib: str, n: int, reps: int, side: int = 0) -> Dict[str, float]:
+    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps, side=side)
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     if res.returncode != 0:
         raise RuntimeError(f"timing failed for {lib}:\n{res.stderr[-2000:]}")
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
+def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int = 0) -> dict:
     base = B.plan_table_entry(n)
     plans = candidate_plans(n, 2 if quick else 3)
     knobs = []
@@ -174,7 +174,7 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log) -> dict:
     results = []
     for p, lib in zip(variants, libs):
         try:
-            t = time_variant(lib, n, 200 if n <= 5000 else 40)
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side)
         except Exception as e:  # a variant that does not launch (resources) is skipped
             log(f"  skip {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={p['kstage']}: "
                 f"{str(e).splitlines()[-1][:120]}")
@@ -216,6 +216,9 @@ def main() -> None:
     ap.add_argument("--jobs", type=int, default=0)
     ap.add_argument("--out", default=TUNED_JSON)
     ap.add_argument("--log", default=None)
+    ap.add_argument("--map-side", type=int, default=0,
+                    help="time maps of this side (PSF 541^2) instead of N - 540, to compare "
+                         "padded lengths for one workload")
     args = ap.parse_args()
     jobs = args.jobs or (os.cpu_count() or 1)
     logf = open(args.log, "a") if args.log else None
@@ -235,7 +238,7 @@ def main() -> None:
         with open(args.out) as fh:
             table = json.load(fh)
     for n in args.sizes:
-        table[str(n)] = tune_size(n, args.quick, jobs, common, log)
+        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side)
         with open(args.out, "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
     log(f"wrote {args.out}")

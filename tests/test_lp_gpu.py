@@ -6,6 +6,9 @@ workloads, 4096 seeded pixels plus the 64 brightest pixels of the GPU
 output (so that the denominator is the global maximum).
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -31,7 +34,18 @@ def ctx():
 def err_maxnorm(got, ref):
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
-    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    record_error(err)
+    return err
+
+
+def record_error(err):
+    """Append the measured error to $LP_PARITY_LOG (one JSON line per check)."""
+    path = os.environ.get("LP_PARITY_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0],
+                                 "max_norm_err": err}) + "\n")
 
 
 def dev(a):
@@ -200,6 +214,30 @@ def test_host_entry_point_matches_device(ctx):
     lp.lp_sync_status(ctx)
     assert torch.equal(out_h, out_d.cpu())
     lp.lp_spectrum_release(ctx, s)
+
+
+def test_host_entry_point_banded_ragged_full_mode(ctx):
+    """The pipelined host path (row bands copied while transformed) on an odd
+    map size, FULL output, three spectra (one complex), leading dimensions."""
+    g = np.random.default_rng(16)
+    big = g.lognormal(0.0, 1.0, (77, 130)).astype(np.float32)
+    L = big[:, 3:120]                                     # 77 x 117, ldl = 130
+    Ks = [synth.psf_power_exp(21, 1.0, 0.25, 1.25, 40.0), g.uniform(0.1, 1.0, (21, 21)),
+          synth.psf_power_exp(21, 1.0, 0.25, 2.0, 80.0)]
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=77, max_w=117) for K in Ks]
+    Ho, Wo = 77 + 20, 117 + 20
+    host_out = [np.full((Ho, Wo + 5), np.nan, np.float32) for _ in Ks]
+    lp.lp_map_host(ctx, L, specs, [o[:, :Wo] for o in host_out], mode=lp.LP_OUT_FULL)
+    lp.lp_sync_status(ctx)
+    dev_out = [torch.empty((Ho, Wo), dtype=torch.float32, device=DEV) for _ in Ks]
+    lp.lp_map(ctx, dev(np.ascontiguousarray(L)), specs, dev_out, mode=lp.LP_OUT_FULL)
+    lp.lp_sync_status(ctx)
+    for k, K in enumerate(Ks):
+        np.testing.assert_array_equal(host_out[k][:, :Wo], dev_out[k].cpu().numpy())
+        assert np.isnan(host_out[k][:, Wo:]).all()
+        assert err_maxnorm(host_out[k][:, :Wo], oracle.conv_full(np.ascontiguousarray(L), K)) <= TOL_FP32
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
 
 
 # --- full-size workloads, sampled against the oracle -------------------------
