@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true",
+                    help="skip the torch.fft (cuFFT) comparator")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU-oracle sample")
@@ -283,6 +285,40 @@ def workload_config(wl, pad):
 # our arm
 # ----------------------------------------------------------------------------
 
+def cufft_comparator(L, Ks, ny, nx, flush, steps, stream):
+    import torch
+    H, W = L.shape
+    dev = L.device
+    khs = []
+    for K in Ks:
+        hk, wk = K.shape
+        Kd = torch.from_numpy(K).to(dev)
+        Kw = torch.roll(torch.nn.functional.pad(Kd, (0, nx - wk, 0, ny - hk)),
+                        shifts=(-(hk // 2), -(wk // 2)), dims=(0, 1))
+        khs.append(torch.fft.rfft2(Kw).to(torch.complex64))
+    outs = [None] * len(Ks)
+
+    def step():
+        Lh = torch.fft.rfft2(L, s=(ny, nx))
+        for k, kh in enumerate(khs):
+            outs[k] = torch.fft.irfft2(Lh * kh, s=(ny, nx))[:H, :W]
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        e0[i].record(stream)
+        step()
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
+    return {"value": H * W * len(Ks) / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "what": "torch.fft rfft2 (zero-padded) x spectrum -> irfft2 -> crop, FP32, same workload"}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -385,6 +421,13 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": 4 * H * W * n, "steps": args.e2e_steps,
                "host_memory": "pinned"}
 
+    # comparator (bench only, not the product path): the same map through
+    # torch.fft, i.e. cuFFT -- zero-padded rfft2, product with the spectrum of
+    # the wrap-placed PSF, irfft2, crop
+    cufft = None
+    if not args.no_cufft:
+        cufft = cufft_comparator(L, Ks, ny, nx, flush, min(args.steps, 200), stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npx, secs, cores = oracle_rate(L_host, Ks[0], args.cpu_seconds, wl.seed + 7)
@@ -414,6 +457,7 @@ def run_ours(args, rank, world, local_rank):
         "whole_step_gbs": sum(model.values()) / (dev_ms / args.steps / 1e3) / 1e9 / world,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": sum(passes[p][1] for p in PASSES),
+        "cufft_comparator": cufft,
         "spectrum_build_ms": s0_ms, "wall_s": wall_s,
     }
     print(json.dumps(line), flush=True)

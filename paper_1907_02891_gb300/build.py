@@ -118,7 +118,7 @@ def plan_table_entry(n: int) -> dict:
             f = cand
             break
     return dict(radices=list(r), threads=t, f1=f, f3=f, smem=smem,
-                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True, tt=0)
+                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True, tt=0, pf=[1, 1, 1], db=[0, 0, 0])
 
 
 def plan_table() -> Dict[int, dict]:
@@ -135,7 +135,8 @@ def plan_table() -> Dict[int, dict]:
         if t:
             e.update(radices=list(t["radices"]), threads=threads_for(n, t["radices"]),
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
-                     tt=int(t.get("tt", 0)))
+                     tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
+                     db=list(t.get("db", [0, 0, 0])))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -159,6 +160,9 @@ constexpr long long kMaxSmem = 227 * 1024;
 constexpr int kUPB1 = {upb1}, kUPB2 = {upb2}, kUPB3 = {upb3};
 constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
 constexpr bool kKSTAGE = {kstage};
+constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
+constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
+constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
 
 template <class K>
 cudaError_t attr(K k, int bytes)
@@ -173,8 +177,8 @@ cudaError_t set_attrs()
 {{
     cudaError_t e;
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, false>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, false>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
     if constexpr (kSmem2 <= kMaxSmem) {{
         if ((e = attr(p2_cols<P, kN, true, true>, kSmem2)) != cudaSuccess) return e;
         if ((e = attr(p2_cols<P, kN, false, true>, kSmem2)) != cudaSuccess) return e;
@@ -182,17 +186,17 @@ cudaError_t set_attrs()
         if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
     }}
     if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE>, (int)kMaxSmem)) != cudaSuccess) return e;
-    return attr(p3_rows_pf<P, kN, kUPB3, kMINB3>, (int)kMaxSmem);
+    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    return attr(p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3>, (int)kMaxSmem);
 }}
 
 cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
-    const long long sm = kSmem + p1_stage_bytes(a.Wst);
-    if (sm <= kMaxSmem) {{
-        p1_rows_pf<P, kN, kUPB1, kMINB1><<<persistent_grid(a.npairs - a.pair0, kUPB1), P::T, sm, s>>>(a);
+    const long long sm = kX1 * kSmem + p1_stage_bytes(a.Wst);
+    if (kPF1 && sm <= kMaxSmem) {{
+        p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1><<<persistent_grid(a.npairs - a.pair0, kUPB1), P::T, sm, s>>>(a);
     }} else {{
         p1_rows<P, kN, kF1><<<(a.npairs - a.pair0 + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
     }}
@@ -202,16 +206,16 @@ cudaError_t p1(const P1Args& a, cudaStream_t s)
 cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 {{
     const bool multi = a.nspec > 1;
-    const long long sm = kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal, kKSTAGE);
+    const long long sm = kX2 * kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal, kKSTAGE);
     if (!multi) {{
-        if (sm <= kMaxSmem) {{
+        if (kPF2 && sm <= kMaxSmem) {{
             if (kreal)
-                p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
+                p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
             else
-                p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
+                p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
         }} else {{
-            if (kreal) p2_cols<P, kN, true, false><<<a.ncols, P::T, kSmem, s>>>(a);
-            else p2_cols<P, kN, false, false><<<a.ncols, P::T, kSmem, s>>>(a);
+            if (kreal) p2_cols<P, kN, true, false, kMINB2, kDB2><<<a.ncols, P::T, kX2 * kSmem, s>>>(a);
+            else p2_cols<P, kN, false, false, kMINB2, kDB2><<<a.ncols, P::T, kX2 * kSmem, s>>>(a);
         }}
         return cudaGetLastError();
     }}
@@ -246,9 +250,9 @@ cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 
 cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
-    const long long sm = kSmem + p3_stage_bytes(a.ncols);
-    if (sm <= kMaxSmem) {{
-        p3_rows_pf<P, kN, kUPB3, kMINB3><<<dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec), P::T, sm, s>>>(a);
+    const long long sm = kX3 * kSmem + p3_stage_bytes(a.ncols);
+    if (kPF3 && sm <= kMaxSmem) {{
+        p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3><<<dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec), P::T, sm, s>>>(a);
     }} else {{
         p3_rows<P, kN, kF3><<<dim3((a.npairs - a.pair0 + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
     }}
@@ -272,6 +276,10 @@ const int kNumSizes = {count};
 """
 
 
+def _b(x) -> str:
+    return "true" if x else "false"
+
+
 def _write_if_changed(path: str, text: str) -> None:
     if os.path.exists(path):
         with open(path) as fh:
@@ -292,6 +300,8 @@ def generate() -> List[str]:
                                upb1=p["upb"][0], upb2=p["upb"][1], upb3=p["upb"][2],
                                minb1=p["minb"][0], minb2=p["minb"][1], minb3=p["minb"][2],
                                kstage="true" if p["kstage"] else "false",
+                               pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
+                               db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

@@ -97,6 +97,11 @@ struct Plan {
     static_assert(T <= 1024, "too many threads per transform");
     using FwdChain = Chain<N, -1, 1, 0, T, Fwd>;
     using InvChain = Chain<N, +1, 1, 0, T, Inv>;
+    // double-buffered chains: the inverse continues the forward's buffer
+    // alternation (it follows the forward's exchanges in the column pass)
+    static constexpr int NEX = SeqInfo<Fwd>::stages - 1;   // exchanges per chain
+    using FwdChainDB = Chain<N, -1, 1, 0, T, Fwd, true, 0>;
+    using InvChainDB = Chain<N, +1, 1, 0, T, Inv, true, NEX % 2>;
     static constexpr int E0 = FwdChain::E;                    // forward first stage
     static constexpr int EL = Chain<N, -1, N / RL, 0, T, Seq<RL>>::E;  // forward last stage
     static constexpr int EI = InvChain::E;                    // inverse first stage (= EL)
@@ -282,9 +287,12 @@ __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, con
     });
 }
 
-template <class P, int N, bool KREAL, bool MULTI>
-__global__ void __launch_bounds__(P::T) p2_cols(const __grid_constant__ P2Args a)
+template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false>
+__global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2Args a)
 {
+    static_assert(!(DB && MULTI), "the batched column pass is single-buffered");
+    using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
+    using Inv = typename std::conditional<DB, typename P::InvChainDB, typename P::InvChain>::type;
     extern __shared__ float2 smem2[];
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(P::T) p2_cols(const __grid_constant__ P2Args a
             v[e][m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
         }
     }
-    P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
+    Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
         if constexpr (MULTI) {
             float2* F = smem2 + P::SMEM_ELEMS;  // parked forward column
 #pragma unroll
@@ -320,11 +328,11 @@ __global__ void __launch_bounds__(P::T) p2_cols(const __grid_constant__ P2Args a
             spectrum_product<P, N, KREAL, false>(fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * kw,
                                                  nullptr);
             float2* Uc = a.U + (long long)c * a.ldU;
-            P::InvChain::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
+            Inv::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
                 store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
-            });
+            }, P::SMEM_ELEMS);
         }
-    });
+    }, P::SMEM_ELEMS);
 }
 
 // ---------------------------------------------------------------------------
@@ -400,14 +408,16 @@ __host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long 
 }
 __host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll * ncols; }
 
-template <class P, int N, int UPB, int MINB>
+template <class P, int N, int UPB, int MINB, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
+    constexpr int NBUF = DB ? 2 : 1;
+    using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
     float2* sm = smem2;
-    float* st = reinterpret_cast<float*>(smem2 + P::SMEM_ELEMS);  // rows a, b: 2 x Wst floats
+    float* st = reinterpret_cast<float*>(smem2 + NBUF * P::SMEM_ELEMS);  // rows a, b: 2 x Wst floats
     const int Wst = a.Wst;
 
     auto prefetch = [&](int pair) {
@@ -446,10 +456,10 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
         }
         __syncthreads();  // staging consumed
         prefetch(pair + gridDim.x);
-        P::FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[P::EL][P::RL], int tt) {
+        Fwd::run(v, t, sm, a.tw, [&](float2(&z)[P::EL][P::RL], int tt) {
             to_smem_natural<P, N>(z, tt, sm);
             unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
-        });
+        }, P::SMEM_ELEMS);
     };
     prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 
 // single spectrum; T column staged, K^ column staged when KSTAGE (else read
 // directly at the product)
-template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE>
+template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 {
     extern __shared__ float2 smem2[];
@@ -468,8 +478,11 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL;
     constexpr int KW = KREAL ? 1 : 2;                    // floats per K^ element
+    constexpr int NBUF = DB ? 2 : 1;
+    using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
+    using Inv = typename std::conditional<DB, typename P::InvChainDB, typename P::InvChain>::type;
     float2* sm = smem2;
-    float2* tst = smem2 + P::SMEM_ELEMS;                 // ldT complex
+    float2* tst = smem2 + NBUF * P::SMEM_ELEMS;          // ldT complex
     float* kst = reinterpret_cast<float*>(tst + a.ldT);  // ldK floats or complex
 
     auto prefetch_t = [&](int c) {
@@ -503,7 +516,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
         }
         __syncthreads();
         prefetch_t(c + gridDim.x);
-        P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
+        Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
             spectrum_product<P, N, KREAL, KSTAGE>(
                 fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW, kst);
             if constexpr (KSTAGE) {
@@ -511,10 +524,10 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
                 prefetch_k(c + gridDim.x);
             }
             float2* Uc = a.U + (long long)c * a.ldU;
-            P::InvChain::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
+            Inv::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
                 store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
-            });
-        });
+            }, P::SMEM_ELEMS);
+        }, P::SMEM_ELEMS);
     };
     prefetch_t(blockIdx.x);
     prefetch_k(blockIdx.x);
@@ -524,14 +537,16 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     });
 }
 
-template <class P, int N, int UPB, int MINB>
+template <class P, int N, int UPB, int MINB, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 {
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int RI = P::RL, NBI = N / RI;
+    constexpr int NBUF = DB ? 2 : 1;
+    using Inv = typename std::conditional<DB, typename P::InvChainDB, typename P::InvChain>::type;
     float2* sm = smem2;
-    float4* ust = reinterpret_cast<float4*>(smem2 + P::SMEM_ELEMS);  // ncols x {A, B}
+    float4* ust = reinterpret_cast<float4*>(smem2 + NBUF * P::SMEM_ELEMS);  // ncols x {A, B}
     const int sidx = blockIdx.y;
     const float4* Uq = reinterpret_cast<const float4*>(a.U + (long long)sidx * a.specU);
     const long long ldq = a.ldU / 2;
@@ -562,10 +577,10 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
         }
         __syncthreads();
         prefetch(pair + gridDim.x);
-        P::InvChain::run(v, t, sm, a.tw, [&](float2(&o)[P::EJ][P::R0], int tt) {
+        Inv::run(v, t, sm, a.tw, [&](float2(&o)[P::EJ][P::R0], int tt) {
             float* oa = a.out[sidx] + (long long)ra * a.ldo;
             store_rows<P, N>(o, tt, oa, oa + a.ldo, vb, a.c0, a.Wout);
-        });
+        }, P::SMEM_ELEMS);
     };
     prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {

@@ -390,16 +390,22 @@ template <int... Rs> struct ChainExtent<Seq<Rs...>> {
 // outputs (v[e] holds y[j + m N/R_last]) to `fin(v, t)`.
 // Every thread of the block must call it (it contains barriers).
 // ---------------------------------------------------------------------------
-template <int N, int DIR, int Ns, int SIdx, int TT, class S> struct Chain;
+// Double buffering (DB): exchange number x of the block's sequence uses
+// buffer (BUF + x) mod 2 (sm and sm + bstride).  Consecutive exchanges then
+// use different buffers, so the write of an exchange only has to wait for
+// the readers of the exchange two before it -- which finished before the
+// previous exchange's barrier -- and one barrier per exchange suffices.
+template <int N, int DIR, int Ns, int SIdx, int TT, class S, bool DB = false, int BUF = 0> struct Chain;
 
-template <int N, int DIR, int Ns, int SIdx, int TT, int R, int... Rest>
-struct Chain<N, DIR, Ns, SIdx, TT, Seq<R, Rest...>> {
+template <int N, int DIR, int Ns, int SIdx, int TT, int R, int... Rest, bool DB, int BUF>
+struct Chain<N, DIR, Ns, SIdx, TT, Seq<R, Rest...>, DB, BUF> {
     static constexpr int NB = N / R;
     static constexpr int E = (NB + TT - 1) / TT;
+    static constexpr int EXCHANGES = sizeof...(Rest);
 
     template <class Fin>
     __device__ __forceinline__ static void run(float2 (&v)[E][R], int t, float2* sm,
-                                               const TwChain& tw, Fin&& fin)
+                                               const TwChain& tw, Fin&& fin, int bstride = 0)
     {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -425,19 +431,20 @@ struct Chain<N, DIR, Ns, SIdx, TT, Seq<R, Rest...>> {
         if constexpr (sizeof...(Rest) == 0) {
             fin(v, t);
         } else {
-            using Next = Chain<N, DIR, Ns * R, SIdx + 1, TT, Seq<Rest...>>;
+            using Next = Chain<N, DIR, Ns * R, SIdx + 1, TT, Seq<Rest...>, DB, BUF>;
+            float2* xb = (DB && ((BUF + SIdx) & 1)) ? sm + bstride : sm;
             constexpr int R2 = SeqInfo<Seq<Rest...>>::first;
             constexpr int NB2 = N / R2;
             constexpr int P = Ns * R;
             constexpr int q = pad_q(Ns, R);
             static_assert(NB2 % P == 0, "reader stride must be a multiple of the group size");
             constexpr int rstride = NB2 + q * (NB2 / P);
-            __syncthreads();  // earlier readers of sm are done
+            if constexpr (!DB) __syncthreads();  // earlier readers of sm are done
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = t + e * TT;
                 if (j < NB) {
-                    float2* w0 = sm + (j / Ns) * (P + q) + (j % Ns);
+                    float2* w0 = xb + (j / Ns) * (P + q) + (j % Ns);
 #pragma unroll
                     for (int m = 0; m < R; ++m) w0[m * Ns] = v[e][m];
                 }
@@ -448,12 +455,12 @@ struct Chain<N, DIR, Ns, SIdx, TT, Seq<R, Rest...>> {
             for (int e = 0; e < Next::E; ++e) {
                 const int j = t + e * TT;
                 if (j < NB2) {
-                    const float2* r0 = sm + j + q * (j / P);
+                    const float2* r0 = xb + j + q * (j / P);
 #pragma unroll
                     for (int m = 0; m < R2; ++m) w[e][m] = r0[m * rstride];
                 }
             }
-            Next::run(w, t, sm, tw, fin);
+            Next::run(w, t, sm, tw, fin, bstride);
         }
     }
 };

@@ -77,6 +77,8 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
                              upb1=plan["upb"][0], upb2=plan["upb"][1], upb3=plan["upb"][2],
                              minb1=plan["minb"][0], minb2=plan["minb"][1], minb3=plan["minb"][2],
                              kstage="true" if plan["kstage"] else "false",
+                             pf1=B._b(plan["pf"][0]), pf2=B._b(plan["pf"][1]), pf3=B._b(plan["pf"][2]),
+                             db1=B._b(plan["db"][0]), db2=B._b(plan["db"][1]), db3=B._b(plan["db"][2]),
                              rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
     src = os.path.join(d, f"size_{n}.cu")
     with open(src, "w") as fh:
@@ -147,10 +149,15 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
     base = B.plan_table_entry(n)
     plans = candidate_plans(n, 2 if quick else 3)
     knobs = []
-    for upb, minb, kst in itertools.product((1, 2), (1, 2, 3), (False, True)):
+    for upb, minb, kst in itertools.product((1, 2, 3), (1, 2, 3), (False, True)):
         if quick and (minb == 3 and upb == 1):
             continue
-        knobs.append((upb, minb, kst))
+        if upb == 3 and (quick or kst):
+            continue
+        knobs.append((upb, minb, kst, 1))
+    knobs.append((1, 1, False, 0))   # one-unit-per-block kernels (no prefetch)
+    knobs.append((1, 2, False, 0))
+    knobs.append((1, 3, False, 0))
     variants = []
     for r in plans:
         # threads per transform: one butterfly per thread in every stage (0),
@@ -160,12 +167,12 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
         if few < B.threads_for(n, r):
             tts.append(few)
         for tt in tts:
-            for upb, minb, kst in knobs:
-                if tt and kst:          # staging only varies at the default thread count
+            for upb, minb, kst, pf in knobs:
+                if tt and (kst or not pf):   # staging / no-prefetch only at the default thread count
                     continue
                 p = dict(base)
                 p.update(radices=list(r), threads=tt or B.threads_for(n, r), upb=[upb] * 3,
-                         minb=[minb] * 3, kstage=kst, tt=tt)
+                         minb=[minb] * 3, kstage=kst, tt=tt, pf=[pf] * 3, db=[0, 0, 0])
                 variants.append(p)
     t0 = time.time()
     with cf.ThreadPoolExecutor(jobs) as ex:
@@ -180,7 +187,7 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
                 f"{str(e).splitlines()[-1][:120]}")
             continue
         results.append((p, t))
-        log(f"  {p['radices']} tt={p['tt']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
+        log(f"  {p['radices']} tt={p['tt']} pf={p['pf'][0]} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
             + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
     if not results:
         raise RuntimeError(f"no variant of {n} ran")
@@ -203,9 +210,37 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
     out.update(radices=list(r), threads=tt or B.threads_for(n, r), tt=tt,
                upb=[choice["p1_rows"]["upb"][0], choice["p2_cols"]["upb"][1], choice["p3_rows"]["upb"][2]],
                minb=[choice["p1_rows"]["minb"][0], choice["p2_cols"]["minb"][1], choice["p3_rows"]["minb"][2]],
-               kstage=choice["p2_cols"]["kstage"], tuned_total_us=total * 1e3)
-    log(f"N={n}: chose {out['radices']} tt={out['tt']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
+               kstage=choice["p2_cols"]["kstage"], tuned_total_us=total * 1e3,
+               pf=[choice["p1_rows"]["pf"][0], choice["p2_cols"]["pf"][1], choice["p3_rows"]["pf"][2]])
+    log(f"N={n}: chose {out['radices']} tt={out['tt']} pf={out['pf']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
         f"(sum of best passes {total * 1e3:.1f} us)")
+    # refinement: double-buffered exchange on top of the choice, with each
+    # resident-block setting; kept per pass where it is faster
+    best_pass = {name: min(t[name] for p, t in results if tuple(p["radices"]) == tuple(out["radices"])
+                           and p["tt"] == out["tt"] and p["upb"][i] == out["upb"][i] and p["pf"][i] == out["pf"][i]
+                           and p["minb"][i] == out["minb"][i] and (i != 1 or p["kstage"] == out["kstage"]))
+                 for i, name in enumerate(("p1_rows", "p2_cols", "p3_rows"))}
+    refine = []
+    for minb in (1, 2, 3):
+        p = dict(out)
+        p.update(db=[1, 1, 1], minb=[minb] * 3)
+        refine.append(p)
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        rlibs = list(ex.map(lambda p: _variant_lib(n, p, common), refine))
+    db, minb = [0, 0, 0], list(out["minb"])
+    for p, lib in zip(refine, rlibs):
+        try:
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side)
+        except Exception as e:
+            log(f"  skip db=1 minb={p['minb'][0]}: {str(e).splitlines()[-1][:120]}")
+            continue
+        log(f"  db=1 minb={p['minb'][0]}: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+        for i, name in enumerate(("p1_rows", "p2_cols", "p3_rows")):
+            if t[name] < best_pass[name] * 0.99:
+                best_pass[name] = t[name]
+                db[i], minb[i] = 1, p["minb"][0]
+    out.update(db=db, minb=minb, tuned_total_us=sum(best_pass.values()) * 1e3)
+    log(f"N={n}: refined db={db} minb={minb} (sum {out['tuned_total_us']:.1f} us)")
     return out
 
 
