@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the CPU-oracle sample")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "split_bf16"],
+                    help="column-pass precision: FP32 FFT stages, or the DFT stages as "
+                         "split-BF16 (hi/lo) products on the tensor cores")
     ap.add_argument("--mode", default="map", choices=["map", "serve"],
                     help="map: the throughput line; serve: the request-scheduler run")
     ap.add_argument("--requests", type=int, default=2000)
@@ -340,11 +343,15 @@ def run_ours(args, rank, world, local_rank):
     ctx = lp.lp_create(local_rank)
     stream = torch.cuda.current_stream()
     L = torch.from_numpy(L_host).to(dev)
+    prec = lp.LP_PREC_SPLIT_BF16 if args.prec == "split_bf16" else lp.LP_PREC_FP32
     t0 = time.perf_counter()
     # one padded size for all PSFs: the largest PSF's N_L + N_K - 1, rounded up
+    # (for the split precision, to a column length that has that pass)
     ny = lp.lp_supported_size(H + hk_max - 1)
+    if prec == lp.LP_PREC_SPLIT_BF16:
+        ny = min(n_ for n_ in lp.supported_sizes() if n_ >= H + hk_max - 1 and lp.lp_split_supported(n_))
     nx = lp.lp_supported_size(W + hk_max - 1)
-    specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), pad_ny=ny, pad_nx=nx)
+    specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), pad_ny=ny, pad_nx=nx, prec=prec)
              for K in Ks]
     torch.cuda.synchronize()
     s0_ms = 1e3 * (time.perf_counter() - t0) / n
@@ -356,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         flush.zero_()
-        lp.lp_map(ctx, L, specs, outs)
+        lp.lp_map(ctx, L, specs, outs, prec=prec)
     lp.lp_sync_status(ctx)
     lp.lp_set_pass_timing(ctx, True)
     lp.lp_get_pass_timing(ctx)
@@ -372,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record(stream)
-        lp.lp_map(ctx, L, specs, outs)
+        lp.lp_map(ctx, L, specs, outs, prec=prec)
         ev1[k].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -403,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
         Lh = torch.from_numpy(L_host).pin_memory()
         oh = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(n)]
         for _ in range(3):
-            lp.lp_map_host(ctx, Lh, specs, oh)
+            lp.lp_map_host(ctx, Lh, specs, oh, prec=prec)
         lp.lp_sync_status(ctx)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -412,7 +419,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            lp.lp_map_host(ctx, Lh, specs, oh)
+            lp.lp_map_host(ctx, Lh, specs, oh, prec=prec)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
@@ -443,8 +450,10 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config(wl, (ny, nx)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == lp.LP_PREC_FP32 else "bf16-split (hi/lo) products, f32 accumulate",
+        "data": "synthetic", "config": dict(workload_config(wl, (ny, nx)),
+                       **({} if prec == lp.LP_PREC_FP32 else {"precision": args.prec})),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic,

@@ -59,8 +59,9 @@ typedef enum lp_status {
 
 typedef enum lp_precision {
     LP_PREC_FP32 = 0,       /* FP32 FFT path */
-    LP_PREC_SPLIT_BF16 = 1, /* reserved: split-BF16 tensor-core DFT stages */
-    LP_PREC_SPLIT_FP16 = 2  /* reserved: split-FP16 tensor-core DFT stages */
+    LP_PREC_SPLIT_BF16 = 1, /* column DFT stages on the tensor cores: operands split
+                               into BF16 hi + lo, FP32 accumulation (row passes FP32) */
+    LP_PREC_SPLIT_FP16 = 2  /* reserved: split-FP16 tensor-core DFT stages (not built) */
 } lp_precision;
 
 typedef enum lp_outmode {
@@ -99,6 +100,16 @@ int lp_supported_size_at(int i);
 int lp_supported_size(int n);
 
 /*
+ * 1 if the supported length n has the split-precision (LP_PREC_SPLIT_BF16)
+ * column pass, else 0.  That precision needs it for the padded column count
+ * pad_ny; its auto padding picks the smallest such length.  The pass runs
+ * each radix-R stage of the column DFT (Eq. (10)) as a real 2R x 2R matrix
+ * product on the tensor cores, D = A_hi F_hi + A_hi F_lo + A_lo F_hi, and
+ * matches the FP32 path to about 1e-5 of the map maximum.
+ */
+int lp_split_supported(int n);
+
+/*
  * Kernel spectrum (Sec. 2.3 Eq. (9)-(10), padding of Sec. 2.5): the DFT of
  * K zero-padded to pad_ny x pad_nx, computed in FP64 on the device and kept
  * device-resident in FP32, scaled so that lp_map returns Eq. (7) directly.
@@ -109,7 +120,9 @@ int lp_supported_size(int n);
  *              pad_ny / pad_nx is 0 (auto = smallest supported size
  *              >= max_h + hk - 1, resp. max_w + wk - 1).
  *   pad_ny/nx  explicit padded size (must be supported), or 0 for auto.
- *   prec       LP_PREC_FP32 (others: LP_ERR_UNSUPPORTED in this build).
+ *   prec       LP_PREC_FP32 or LP_PREC_SPLIT_BF16 (needs lp_split_supported(pad_ny));
+ *              LP_PREC_SPLIT_FP16: LP_ERR_UNSUPPORTED.  lp_map must be called
+ *              with the spectra's precision.
  *   stream     the spectrum is ready in stream order; the call itself
  *              synchronises the stream once (symmetry check).
  *   out        receives a handle (refcounted: an identical request --
@@ -148,7 +161,9 @@ lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s);
  *            LP_OUT_FULL mode they must also share (hk, wk).
  *   out      n device FP32 pointers, caller-allocated: h x w (SAME) or
  *            (h+hk-1) x (w+wk-1) (FULL), leading dimension ldo.
- *   prec     LP_PREC_FP32.
+ *   prec     LP_PREC_FP32, or LP_PREC_SPLIT_BF16 with spectra built in that
+ *            precision (the column pass then runs on the tensor cores, one
+ *            launch per spectrum; the row passes stay FP32).
  * Asynchronous on `stream`; use lp_sync_status to wait and collect device
  * anomalies.  Calls on different streams of one context may overlap; each
  * stream gets its own workspace.
@@ -171,7 +186,8 @@ lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w, int ldl,
  * Multi-class sources, Sec. 2.2 Eq. (4): B = sum_t K_t * L_t for T maps
  * (device FP32, each h x w with leading dimension ldl) and T spectra (same
  * rules as lp_map).  The spectrum products are summed before one inverse
- * transform.  out: device FP32, leading dimension ldo.
+ * transform.  out: device FP32, leading dimension ldo.  Only LP_PREC_FP32 is
+ * built here (other precisions: LP_ERR_UNSUPPORTED).
  */
 lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T, int h, int w, int ldl,
                             const lp_spectrum* const* spectra, float* out, int ldo,

@@ -146,6 +146,7 @@ def plan_table() -> Dict[int, dict]:
 _SIZE_TU = """// generated by paper_1907_02891_gb300/build.py -- one supported FFT length
 #include "conv_kernels.cuh"
 #include "lp_internal.h"
+#include "tc_kernels.cuh"
 
 namespace lpk {{
 namespace {{
@@ -163,6 +164,10 @@ constexpr bool kKSTAGE = {kstage};
 constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
 constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
 constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
+// split-precision tensor-core column pass (0 shared bytes: not available)
+using TP = TcPlan<P, kN>;
+constexpr bool kTC = TP::FITS;
+constexpr int kTcSmem = kTC ? TP::SMEM_BYTES : 0;
 
 template <class K>
 cudaError_t attr(K k, int bytes)
@@ -186,6 +191,10 @@ cudaError_t set_attrs()
         if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
     }}
     if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
+    if constexpr (kTC) {{
+        if ((e = attr(p2_cols_tc<P, kN, true>, kTcSmem)) != cudaSuccess) return e;
+        if ((e = attr(p2_cols_tc<P, kN, false>, kTcSmem)) != cudaSuccess) return e;
+    }}
     if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, (int)kMaxSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
@@ -248,6 +257,35 @@ cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
     }}
 }}
 
+// persistent grid of the tensor-core column pass: resident blocks per SM
+// (shared memory; TMEM columns) times the SMs
+template <bool KREAL>
+int tc_grid(int ncols)
+{{
+    static int cap = 0;
+    if (cap == 0) {{
+        int dev = 0, sms = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2_cols_tc<P, kN, KREAL>, TP::THREADS, kTcSmem);
+        const int tm = 512 / TP::TMEM_COLS;
+        cap = (occ < tm ? occ : tm) * sms;
+        if (cap < 1) cap = 1;
+    }}
+    return ncols < cap ? ncols : cap;
+}}
+
+cudaError_t p2tc(const P2TcArgs& a, bool kreal, cudaStream_t s)
+{{
+    if constexpr (kTC) {{
+        if (kreal) p2_cols_tc<P, kN, true><<<tc_grid<true>(a.a.ncols), TP::THREADS, kTcSmem, s>>>(a);
+        else p2_cols_tc<P, kN, false><<<tc_grid<false>(a.a.ncols), TP::THREADS, kTcSmem, s>>>(a);
+        return cudaGetLastError();
+    }} else {{
+        return cudaErrorNotSupported;
+    }}
+}}
+
 cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
     const long long sm = kX3 * kSmem + p3_stage_bytes(a.ncols);
@@ -261,7 +299,8 @@ cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 }}  // namespace
 
 extern const SizeKernels kSize_{n} = {{kN, {ns}, {{{rad6}}}, P::T, kF1, kF3, kSmem,
-                                       set_attrs, p1, p2, p2m, p3}};
+                                       set_attrs, p1, p2, p2m, p3,
+                                       kTC ? TP::THREADS : 0, kTcSmem, p2tc}};
 }}  // namespace lpk
 """
 

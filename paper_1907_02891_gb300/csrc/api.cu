@@ -20,6 +20,7 @@
 #include "../../include/lp.h"
 #include "conv_kernels.cuh"
 #include "lp_internal.h"
+#include "tc_kernels.cuh"
 #include "lp_runtime.h"
 
 using namespace lpk;
@@ -70,6 +71,23 @@ extern "C" int lp_supported_size(int n)
     for (int i = 0; i < kNumSizes; ++i) {
         const int N = kAllSizes[i]->N;
         if (N >= n && (best < 0 || N < best)) best = N;
+    }
+    return best;
+}
+
+extern "C" int lp_split_supported(int n)
+{
+    const SizeKernels* k = find_size(n);
+    return (k && k->tc_smem > 0) ? 1 : 0;
+}
+
+// smallest length >= n that has the split-precision tensor-core column pass
+static int tc_supported_size(int n)
+{
+    int best = -1;
+    for (int i = 0; i < kNumSizes; ++i) {
+        const int N = kAllSizes[i]->N;
+        if (N >= n && kAllSizes[i]->tc_smem > 0 && (best < 0 || N < best)) best = N;
     }
     return best;
 }
@@ -159,6 +177,68 @@ static void fill_chain_tables(const int* r, int ns, std::vector<float2>& host, s
     }
 }
 
+// BF16 of x, round to nearest even (finite inputs)
+static uint16_t bf16_rn(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+static float bf16_to_float(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+// bytes of the split-BF16 DFT matrices of one chain (hi + lo per stage)
+static size_t tc_chain_bytes(const int* r, int ns)
+{
+    size_t b = 0;
+    for (int s = 0; s < ns; ++s) b += 2ull * ru16(2 * r[s]) * ru16(2 * r[s]) * 2;
+    return b;
+}
+
+// The split-BF16 DFT matrices of a chain for the tensor-core column pass.
+// Stage s (radix R, Kp = 16 ceil(2R / 16)) maps a butterfly's inputs x_q
+// (Re, Im interleaved: columns 2q, 2q+1) to its outputs y_k (rows 2k, 2k+1),
+// y_k = sum_q x_q exp(dir i 2 pi k q / R) (Eq. (10) of radix R), as the
+// real Kp x Kp matrix with blocks [c -s; s c], c + i s = exp(dir i 2 pi kq/R),
+// zero elsewhere.  Each matrix is stored as hi = bf16(M) then
+// lo = bf16(M - hi), element (n, k) at ((n / 8) (Kp / 8) + k / 8) 64 +
+// (n mod 8) 8 + k mod 8 (8 x 8 core matrices, K-major).
+static void fill_tc_mats(const int* r, int ns, int dir, uint16_t* dst)
+{
+    for (int s = 0; s < ns; ++s) {
+        const int R = r[s], KP = ru16(2 * R), KG = KP / 8;
+        std::vector<double> M((size_t)KP * KP, 0.0);
+        for (int k = 0; k < R; ++k)
+            for (int q = 0; q < R; ++q) {
+                const double th = 2.0 * M_PI * (double)((k * q) % R) / (double)R;
+                const double c = std::cos(th), sn = dir * std::sin(th);
+                M[(size_t)(2 * k) * KP + 2 * q] = c;
+                M[(size_t)(2 * k) * KP + 2 * q + 1] = -sn;
+                M[(size_t)(2 * k + 1) * KP + 2 * q] = sn;
+                M[(size_t)(2 * k + 1) * KP + 2 * q + 1] = c;
+            }
+        uint16_t* hi = dst;
+        uint16_t* lo = dst + (size_t)KP * KP;
+        for (int n = 0; n < KP; ++n)
+            for (int k = 0; k < KP; ++k) {
+                const double v = M[(size_t)n * KP + k];
+                const uint16_t h = bf16_rn((float)v);
+                const uint16_t l = bf16_rn((float)(v - (double)bf16_to_float(h)));
+                const size_t off = ((size_t)(n / 8) * KG + k / 8) * 64 + (n % 8) * 8 + (k % 8);
+                hi[off] = h;
+                lo[off] = l;
+            }
+        dst += 2ull * KP * KP;
+    }
+}
+
 lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
 {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
@@ -176,18 +256,32 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
         rev[s] = k->radices[ns - 1 - s];
     }
     const size_t nf = chain_table_entries(fwd, ns), nr = chain_table_entries(rev, ns);
-    std::vector<float2> host(nf + nr + 1);
+    // one device block: twiddle tables, then (256-byte aligned) the split
+    // DFT matrices of the tensor-core column pass where this length has one
+    const size_t tw_bytes = (nf + nr + 1) * sizeof(float2);
+    const size_t tc_off = (tw_bytes + 255) / 256 * 256;
+    const size_t tcf = k->tc_smem > 0 ? tc_chain_bytes(fwd, ns) : 0;
+    const size_t tcr = k->tc_smem > 0 ? tc_chain_bytes(rev, ns) : 0;
+    const size_t total = k->tc_smem > 0 ? tc_off + tcf + tcr : tw_bytes;
+    std::vector<unsigned char> host(total, 0);
+    float2* htw = reinterpret_cast<float2*>(host.data());
+    std::vector<float2> tw(nf + nr + 1);
     size_t of[6] = {0}, orv[6] = {0};
-    fill_chain_tables(fwd, ns, host, 0, of);
-    fill_chain_tables(rev, ns, host, nf, orv);
+    fill_chain_tables(fwd, ns, tw, 0, of);
+    fill_chain_tables(rev, ns, tw, nf, orv);
+    std::memcpy(htw, tw.data(), tw.size() * sizeof(float2));
+    if (k->tc_smem > 0) {
+        fill_tc_mats(fwd, ns, -1, reinterpret_cast<uint16_t*>(host.data() + tc_off));
+        fill_tc_mats(rev, ns, +1, reinterpret_cast<uint16_t*>(host.data() + tc_off + tcf));
+    }
     auto rec = std::make_unique<PlanRec>();
     rec->k = k;
-    rec->bytes = host.size() * sizeof(float2);
+    rec->bytes = total;
     void* d = nullptr;
     lp_status st = lp_ctx_alloc(ctx, rec->bytes, &d);
     if (st != LP_OK) return st;
     rec->tw = static_cast<float2*>(d);
-    cudaError_t e = cudaMemcpy(rec->tw, host.data(), rec->bytes, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(d, host.data(), rec->bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         lp_ctx_free(ctx, d, rec->bytes);
         return lp_fail(LP_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e));
@@ -195,6 +289,10 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     for (int s = 0; s < 6; ++s) {
         rec->fwd.p[s] = s < ns ? rec->tw + of[s] : nullptr;
         rec->rev.p[s] = s < ns ? rec->tw + orv[s] : nullptr;
+    }
+    if (k->tc_smem > 0) {
+        rec->tc_fwd = reinterpret_cast<const uint16_t*>(static_cast<char*>(d) + tc_off);
+        rec->tc_inv = reinterpret_cast<const uint16_t*>(static_cast<char*>(d) + tc_off + tcf);
     }
     *out = rec.get();
     ctx->plans.emplace(N, std::move(rec));
@@ -307,14 +405,15 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     if (!ctx || !K || !out) return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: NULL argument");
     if (hk < 1 || wk < 1 || hk % 2 == 0 || wk % 2 == 0)
         return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: PSF sides must be odd and >= 1 (got %d x %d)", hk, wk);
-    if (prec != LP_PREC_FP32)
+    if (prec != LP_PREC_FP32 && prec != LP_PREC_SPLIT_BF16)
         return lp_fail(LP_ERR_UNSUPPORTED, "lp_kernel_spectrum: precision %d is not built", (int)prec);
+    const bool split = prec == LP_PREC_SPLIT_BF16;
     if (pad_ny < 0 || pad_nx < 0 || max_h < 0 || max_w < 0)
         return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: negative size");
     int Ny = pad_ny, Nx = pad_nx;
     if (Ny == 0) {
         if (max_h < 1) return lp_fail(LP_ERR_INVALID, "lp_kernel_spectrum: need max_h or pad_ny");
-        Ny = lp_supported_size(max_h + hk - 1);
+        Ny = split ? tc_supported_size(max_h + hk - 1) : lp_supported_size(max_h + hk - 1);
         if (Ny < 0) return lp_fail(LP_ERR_UNSUPPORTED, "no supported FFT length >= %d", max_h + hk - 1);
     }
     if (Nx == 0) {
@@ -326,6 +425,8 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
         return lp_fail(LP_ERR_UNSUPPORTED, "padded size %d x %d is not a supported FFT length", Ny, Nx);
     if (Ny < hk || Nx < wk)
         return lp_fail(LP_ERR_INVALID, "padded size %d x %d is smaller than the PSF %d x %d", Ny, Nx, hk, wk);
+    if (split && find_size(Ny)->tc_smem == 0)
+        return lp_fail(LP_ERR_UNSUPPORTED, "column length %d has no split-precision tensor-core pass", Ny);
     if (!fft64_supported(Ny) || !fft64_supported(Nx))
         return lp_fail(LP_ERR_UNSUPPORTED, "FP64 spectrum transform cannot factor %d x %d", Ny, Nx);
 
@@ -496,6 +597,7 @@ static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mo
         d->c0 = 0;
     }
     d->ldU = even_up(d->Hout);
+    d->prec = (int)LP_PREC_FP32;
 }
 
 extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
@@ -517,7 +619,8 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     if (ldl < w) return lp_fail(LP_ERR_INVALID, "lp_map: ldl %d < w %d", ldl, w);
     if (n < 1) return lp_fail(LP_ERR_INVALID, "lp_map: need at least one spectrum");
     if (mode != LP_OUT_SAME && mode != LP_OUT_FULL) return lp_fail(LP_ERR_INVALID, "lp_map: bad output mode");
-    if (prec != LP_PREC_FP32) return lp_fail(LP_ERR_UNSUPPORTED, "lp_map: precision %d is not built", (int)prec);
+    if (prec != LP_PREC_FP32 && prec != LP_PREC_SPLIT_BF16)
+        return lp_fail(LP_ERR_UNSUPPORTED, "lp_map: precision %d is not built", (int)prec);
     const lp_spectrum* s0 = spectra[0];
     if (!s0) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum 0 is NULL");
     for (int k = 0; k < n; ++k) {
@@ -536,7 +639,10 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
             return lp_fail(LP_ERR_INVALID, "lp_map: FULL output needs spectra of equal PSF size");
         if (s->prec != prec) return lp_fail(LP_ERR_INVALID, "lp_map: spectrum %d has another precision", k);
     }
+    if (prec == LP_PREC_SPLIT_BF16 && find_size(s0->ny)->tc_smem == 0)
+        return lp_fail(LP_ERR_UNSUPPORTED, "lp_map: column length %d has no split-precision pass", s0->ny);
     map_dims(h, w, s0->ny, s0->nx, s0->hk, s0->wk, mode, d);
+    d->prec = (int)prec;
     if (ldo < d->Wout) return lp_fail(LP_ERR_INVALID, "lp_map: ldo %d < output width %d", ldo, d->Wout);
     return LP_OK;
 }
@@ -570,6 +676,36 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
                                 int cnt, int h, const MapDims& d, const float2* T, float2* U, cudaStream_t st)
 {
     const lp_spectrum* s0 = spectra[0];
+    if (d.prec == (int)LP_PREC_SPLIT_BF16) {
+        // tensor-core column pass: one launch per spectrum
+        for (int i = 0; i < cnt; ++i) {
+            P2TcArgs a2;
+            P2Args& b = a2.a;
+            b.T = T;
+            b.ldT = d.ldT;
+            b.H = h;
+            for (int q = 0; q < kMaxSpectraPerLaunch; ++q) b.K[q] = nullptr;
+            b.K[0] = spectra[base + i]->data;
+            b.ldK = s0->ldK;
+            b.nspec = 1;
+            b.U = U + (size_t)i * d.ncols * d.ldU;
+            b.ldU = d.ldU;
+            b.specU = (long long)d.ncols * d.ldU;
+            b.r0 = d.r0;
+            b.Hout = d.Hout;
+            b.HoutPad = (int)d.ldU;
+            b.ncols = d.ncols;
+            b.twf = py->fwd;
+            b.twi = py->rev;
+            a2.mats_fwd = py->tc_fwd;
+            a2.mats_inv = py->tc_inv;
+            a2.err = ctx->d_err;
+            const int tok = lp_pass_begin(ctx, 1, st);
+            CUDA_TRY(py->k->p2tc(a2, spectra[base + i]->is_real != 0, st));
+            lp_pass_end(ctx, tok, st);
+        }
+        return LP_OK;
+    }
     // the real-spectrum kernel needs every spectrum of the launch real:
     // split the chunk by kind
     int k0 = 0;
@@ -843,6 +979,8 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     for (int t = 0; t < T; ++t)
         if (!L[t]) return lp_fail(LP_ERR_INVALID, "lp_map_multiclass: L[%d] is NULL", t);
     MapDims d;
+    if (prec != LP_PREC_FP32)
+        return lp_fail(LP_ERR_UNSUPPORTED, "lp_map_multiclass: only the FP32 path is built for several classes");
     lp_status st = lp_validate_map(ctx, L[0], h, w, ldl, spectra, T, out, ldo, mode, prec, &d);
     if (st != LP_OK) return st;
     if (mode == LP_OUT_SAME) {

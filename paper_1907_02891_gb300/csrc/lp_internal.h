@@ -17,6 +17,7 @@ struct P1Args;
 struct P2Args;
 struct P3Args;
 struct P2MArgs;
+struct P2TcArgs;
 
 // One supported FFT length with its compiled FP32 kernels.
 struct SizeKernels {
@@ -33,6 +34,11 @@ struct SizeKernels {
     cudaError_t (*p2)(const P2Args&, bool kreal, cudaStream_t);
     cudaError_t (*p2m)(const P2MArgs&, bool kreal, cudaStream_t);
     cudaError_t (*p3)(const P3Args&, int nspec, cudaStream_t);
+    // split-precision (BF16 hi/lo) tensor-core column pass, one spectrum per
+    // launch; tc_smem = 0 where this length has none
+    int tc_threads;
+    int tc_smem;
+    cudaError_t (*p2tc)(const P2TcArgs&, bool kreal, cudaStream_t);
 };
 
 // generated registry (one translation unit per size)

@@ -26,6 +26,10 @@ struct PlanRec {
     float2* tw = nullptr;  // device twiddle tables (forward chain, then reversed chain)
     size_t bytes = 0;
     lpk::TwChain fwd{}, rev{};
+    // split-BF16 DFT matrices of the tensor-core column pass (same block as
+    // tw; null where the length has no such pass)
+    const uint16_t* tc_fwd = nullptr;
+    const uint16_t* tc_inv = nullptr;
 };
 
 struct Workspace {
@@ -39,6 +43,7 @@ struct MapDims {
     long long ldT, ldU; // leading dimensions of T and U (complex elements, even)
     int Hout, Wout;     // output size
     int r0, c0;         // first kept row / column of the circular result
+    int prec;           // lp_precision of the column pass
 };
 
 struct ServeState;

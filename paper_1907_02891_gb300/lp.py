@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "LP_OK", 1: "LP_ERR_INVALID", 2: "LP_ERR_OOM", 3: "LP_ERR_CUD
 # every entry point declared in include/lp.h
 EXPORTS = (
     "lp_version", "lp_last_error", "lp_create", "lp_destroy", "lp_bytes_in_use",
-    "lp_num_supported_sizes", "lp_supported_size_at", "lp_supported_size",
+    "lp_num_supported_sizes", "lp_supported_size_at", "lp_supported_size", "lp_split_supported",
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
     "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
@@ -67,6 +67,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_num_supported_sizes": ([], _i),
         "lp_supported_size_at": ([_i], _i),
         "lp_supported_size": ([_i], _i),
+        "lp_split_supported": ([_i], _i),
         "lp_kernel_spectrum": ([_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
         "lp_spectrum_info": ([_vp] + [ctypes.POINTER(_i)] * 5, _i),
         "lp_spectrum_copy": ([_vp, _vp, _sz, _vp], _i),
@@ -133,6 +134,11 @@ def lp_supported_size_at(i: int) -> int:
 
 def lp_supported_size(n: int) -> int:
     return load_library().lp_supported_size(n)
+
+
+def lp_split_supported(n: int) -> bool:
+    """True if length n has the split-BF16 tensor-core column pass."""
+    return bool(load_library().lp_split_supported(n))
 
 
 def supported_sizes() -> List[int]:

@@ -331,7 +331,7 @@ def test_invalid_arguments(ctx):
         lp.lp_kernel_spectrum(ctx, K, pad_ny=97, pad_nx=96)       # 97 not a built length
     assert e.value.status == lp.LP_ERR_UNSUPPORTED
     with pytest.raises(lp.LpError) as e:
-        lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=50, prec=lp.LP_PREC_SPLIT_BF16)
+        lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=50, prec=lp.LP_PREC_SPLIT_FP16)
     assert e.value.status == lp.LP_ERR_UNSUPPORTED
     s_small = lp.lp_kernel_spectrum(ctx, K, pad_ny=45, pad_nx=64)  # 45 < 40 + 9 - 1
     out = torch.empty((40, 50), dtype=torch.float32, device=DEV)

@@ -1,0 +1,175 @@
+"""GPU parity of the split-precision column pass (LP_PREC_SPLIT_BF16: the
+column DFT stages as BF16 hi/lo matrix products on the tensor cores, FP32
+accumulation) against the FP64 oracle.
+
+Error metric as for the FP32 path: max |B - B_ref| / max |B_ref|.  The bar
+is 2e-4.  Each operand split x = hi + lo leaves a relative residual of
+about 2^-17 and the dropped lo*lo product is of the same order, so one
+stage adds about 1e-5 of its row norm; with up to 3 + 3 column stages and
+the FP32 row passes the bound stays well below 2e-4 of the map maximum.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_02891_gb300 import lp  # noqa: E402
+
+from test_lp_gpu import _sampled_check, dev, err_maxnorm  # noqa: E402
+
+TOL_SPLIT = 2e-4
+DEV = "cuda:0"
+SPLIT = lp.LP_PREC_SPLIT_BF16
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lp.lp_create(0)
+    yield c
+    lp.lp_destroy(c)
+
+
+def run_split(ctx, L, Ks, mode=lp.LP_OUT_SAME, pad=None):
+    h, w = L.shape
+    if pad is None:
+        specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=h, max_w=w, prec=SPLIT) for K in Ks]
+    else:
+        specs = [lp.lp_kernel_spectrum(ctx, dev(K), pad_ny=pad[0], pad_nx=pad[1], prec=SPLIT) for K in Ks]
+    hk, wk = Ks[0].shape
+    shape = lp.output_shape(h, w, hk, wk, mode)
+    outs = [torch.empty(shape, dtype=torch.float32, device=DEV) for _ in Ks]
+    lp.lp_map(ctx, dev(L), specs, outs, mode=mode, prec=SPLIT)
+    lp.lp_sync_status(ctx)
+    res = [o.cpu().numpy() for o in outs]
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+    return res
+
+
+def _split_lengths():
+    return [n for n in lp.supported_sizes() if lp.lp_split_supported(n)]
+
+
+def _split_pairs():
+    sizes = lp.supported_sizes()
+    cols = _split_lengths()
+    return [(ny, sizes[(i * 5 + 2) % len(sizes)]) for i, ny in enumerate(cols)]
+
+
+def test_most_lengths_have_the_split_pass():
+    sizes = lp.supported_sizes()
+    cols = _split_lengths()
+    assert len(cols) >= len(sizes) - 2
+    assert 4704 in cols and 8820 in cols
+
+
+@pytest.mark.parametrize("ny,nx", _split_pairs())
+def test_split_every_column_length(ctx, ny, nx):
+    """Each length with the pass once as the column length; a ragged map
+    inside the padded grid, an asymmetric (complex-spectrum) and a
+    point-symmetric (real-spectrum) PSF, SAME and FULL output."""
+    g = np.random.default_rng(ny * 7919 + nx)
+    hk = 9 if min(ny, nx) >= 40 else 5
+    wk = 7 if min(ny, nx) >= 40 else 3
+    h = min(ny - hk + 1, 97)
+    w = min(nx - wk + 1, 61)
+    L = g.lognormal(0.0, 1.0, (h, w)).astype(np.float32)
+    K = g.uniform(0.05, 1.0, (hk, wk))
+    Ksym = synth.psf_power_exp(hk, 1.0, 0.25, 1.25, 40.0)[:, (hk - wk) // 2:(hk + wk) // 2]
+    mode = lp.LP_OUT_FULL if (ny + nx) % 2 else lp.LP_OUT_SAME
+    B, Bs = run_split(ctx, L, [K, Ksym], mode=mode, pad=(ny, nx))
+    conv = oracle.conv_full if mode == lp.LP_OUT_FULL else oracle.conv_same
+    assert err_maxnorm(B, conv(L, K)) <= TOL_SPLIT
+    assert err_maxnorm(Bs, conv(L, Ksym)) <= TOL_SPLIT
+
+
+def test_split_tall_map_spans_every_row_tile(ctx):
+    """A map as tall as the padded column (several 128-row MMA tiles in every
+    stage, last tile ragged), full map against the oracle."""
+    g = np.random.default_rng(21)
+    L = g.lognormal(0.0, 1.0, (470, 40)).astype(np.float32)
+    K = g.uniform(0.05, 1.0, (31, 9))
+    (B,) = run_split(ctx, L, [K], mode=lp.LP_OUT_FULL, pad=(512, 64))
+    assert err_maxnorm(B, oracle.conv_full(L, K)) <= TOL_SPLIT
+
+
+def test_split_map256_psf101_full_map(ctx):
+    wl = synth.WORKLOADS["map256_psf101"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_split(ctx, L, [K])
+    assert err_maxnorm(B, oracle.conv_same(L, K)) <= TOL_SPLIT
+
+
+def test_split_zero_map_gives_zero(ctx):
+    K = synth.psf_power_exp(21, 1.0, 0.25, 1.25, 40.0)
+    (B,) = run_split(ctx, np.zeros((50, 70), np.float32), [K])
+    assert np.all(B == 0.0)
+
+
+def test_split_map4096_psf541_sampled(ctx):
+    wl = synth.WORKLOADS["map4096_psf541"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_split(ctx, L, [K])
+    assert _sampled_check(L, K, B, wl.seed + 200) <= TOL_SPLIT
+
+
+def test_split_map8192_psf601x16_sampled(ctx):
+    wl = synth.WORKLOADS["map8192_psf601x16"]
+    L, Ks = wl.radiance(), wl.psfs()
+    Bs = run_split(ctx, L, Ks)
+    for k, (K, B) in enumerate(zip(Ks, Bs)):
+        assert _sampled_check(L, K, B, wl.seed + 200 + k, n=256, top=16) <= TOL_SPLIT, k
+
+
+def test_split_host_entry_point_matches_device(ctx):
+    g = np.random.default_rng(22)
+    L = g.lognormal(0.0, 1.0, (77, 117)).astype(np.float32)
+    Ks = [synth.psf_power_exp(21, 1.0, 0.25, 1.25, 40.0), g.uniform(0.1, 1.0, (21, 21))]
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=77, max_w=117, prec=SPLIT) for K in Ks]
+    Ho, Wo = 97, 137
+    host_out = [np.empty((Ho, Wo), np.float32) for _ in Ks]
+    lp.lp_map_host(ctx, L, specs, host_out, mode=lp.LP_OUT_FULL, prec=SPLIT)
+    lp.lp_sync_status(ctx)
+    dev_out = [torch.empty((Ho, Wo), dtype=torch.float32, device=DEV) for _ in Ks]
+    lp.lp_map(ctx, dev(L), specs, dev_out, mode=lp.LP_OUT_FULL, prec=SPLIT)
+    lp.lp_sync_status(ctx)
+    for k, K in enumerate(Ks):
+        np.testing.assert_array_equal(host_out[k], dev_out[k].cpu().numpy())
+        assert err_maxnorm(host_out[k], oracle.conv_full(L, K)) <= TOL_SPLIT
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+
+
+def test_split_precision_rules(ctx):
+    g = np.random.default_rng(23)
+    K = dev(g.uniform(0.1, 1.0, (9, 9)))
+    L = dev(g.lognormal(0.0, 1.0, (40, 40)).astype(np.float32))
+    out = torch.empty((40, 40), dtype=torch.float32, device=DEV)
+    s32 = lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=40)
+    ssp = lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=40, prec=SPLIT)
+    assert s32 != ssp                                     # cached per precision
+    with pytest.raises(lp.LpError) as e:                  # spectrum of the other precision
+        lp.lp_map(ctx, L, [ssp], [out])
+    assert e.value.status == lp.LP_ERR_INVALID
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_map(ctx, L, [s32], [out], prec=SPLIT)
+    assert e.value.status == lp.LP_ERR_INVALID
+    with pytest.raises(lp.LpError) as e:                  # several classes: FP32 only
+        lp.lp_map_multiclass(ctx, [L], [ssp], out, prec=SPLIT)
+    assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_kernel_spectrum(ctx, K, max_h=40, max_w=40, prec=lp.LP_PREC_SPLIT_FP16)
+    assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    no_tc = [n for n in lp.supported_sizes() if not lp.lp_split_supported(n)]
+    if no_tc:
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_kernel_spectrum(ctx, K, pad_ny=no_tc[0], pad_nx=64, prec=SPLIT)
+        assert e.value.status == lp.LP_ERR_UNSUPPORTED
+    lp.lp_sync_status(ctx)
+    lp.lp_spectrum_release(ctx, s32)
+    lp.lp_spectrum_release(ctx, ssp)
