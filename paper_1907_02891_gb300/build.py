@@ -258,19 +258,28 @@ cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 }}
 
 // persistent grid of the tensor-core column pass: resident blocks per SM
-// (shared memory; TMEM columns) times the SMs
+// (registers, shared memory, threads, TMEM columns) times the SMs
 template <bool KREAL>
 int tc_grid(int ncols)
 {{
     static int cap = 0;
     if (cap == 0) {{
-        int dev = 0, sms = 0, occ = 0;
+        int dev = 0, sms = 0, smem_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2_cols_tc<P, kN, KREAL>, TP::THREADS, kTcSmem);
-        const int tm = 512 / TP::TMEM_COLS;
-        cap = (occ < tm ? occ : tm) * sms;
-        if (cap < 1) cap = 1;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa{{}};
+        cudaFuncGetAttributes(&fa, p2_cols_tc<P, kN, KREAL>);
+        const int warps = TP::THREADS / 32;
+        const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        int occ = regs_warp > 0 ? 65536 / (regs_warp * warps) : 1;
+        const int by_smem = smem_sm / (kTcSmem + 1024);
+        const int by_thr = 2048 / TP::THREADS;
+        const int by_tmem = 512 / TP::TMEM_COLS;
+        occ = occ < by_smem ? occ : by_smem;
+        occ = occ < by_thr ? occ : by_thr;
+        occ = occ < by_tmem ? occ : by_tmem;
+        cap = (occ < 1 ? 1 : occ) * sms;
     }}
     return ncols < cap ? ncols : cap;
 }}

@@ -239,6 +239,30 @@ static void fill_tc_mats(const int* r, int ns, int dir, uint16_t* dst)
     }
 }
 
+// bytes of the twiddle step factors of one chain (stages s >= 1)
+static size_t tc_step_bytes(const int* r, int ns)
+{
+    size_t b = 0;
+    for (int s = 1; s < ns; ++s) b += (size_t)r[s - 1] * r[s] * sizeof(float2);
+    return b;
+}
+
+// Step factors of the tensor-core column pass: the next stage's twiddle of
+// output k of a butterfly with slot m is w0 * exp(dir i 2 pi m k / (R_{s-1} R_s)),
+// stored at [m R_{s-1} + k] per stage s >= 1.
+static void fill_tc_steps(const int* r, int ns, int dir, float2* dst)
+{
+    for (int s = 1; s < ns; ++s) {
+        const int Rp = r[s - 1], R = r[s], n = Rp * R;
+        for (int m = 0; m < R; ++m)
+            for (int k = 0; k < Rp; ++k) {
+                const double th = 2.0 * M_PI * (double)((m * k) % n) / (double)n;
+                dst[m * Rp + k] = make_float2((float)std::cos(th), (float)(dir * std::sin(th)));
+            }
+        dst += (size_t)Rp * R;
+    }
+}
+
 lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
 {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
@@ -260,9 +284,13 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     // DFT matrices of the tensor-core column pass where this length has one
     const size_t tw_bytes = (nf + nr + 1) * sizeof(float2);
     const size_t tc_off = (tw_bytes + 255) / 256 * 256;
+    // (matrices of the forward stages -- the inverse chain runs in the
+    // conjugate domain on the same ones --, then the step factors of the
+    // forward and of the reversed chain, both with the forward sign)
     const size_t tcf = k->tc_smem > 0 ? tc_chain_bytes(fwd, ns) : 0;
-    const size_t tcr = k->tc_smem > 0 ? tc_chain_bytes(rev, ns) : 0;
-    const size_t total = k->tc_smem > 0 ? tc_off + tcf + tcr : tw_bytes;
+    const size_t tsf = k->tc_smem > 0 ? tc_step_bytes(fwd, ns) : 0;
+    const size_t tsr = k->tc_smem > 0 ? tc_step_bytes(rev, ns) : 0;
+    const size_t total = k->tc_smem > 0 ? tc_off + (tcf + tsf + tsr + 15) / 16 * 16 : tw_bytes;
     std::vector<unsigned char> host(total, 0);
     float2* htw = reinterpret_cast<float2*>(host.data());
     std::vector<float2> tw(nf + nr + 1);
@@ -272,7 +300,8 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     std::memcpy(htw, tw.data(), tw.size() * sizeof(float2));
     if (k->tc_smem > 0) {
         fill_tc_mats(fwd, ns, -1, reinterpret_cast<uint16_t*>(host.data() + tc_off));
-        fill_tc_mats(rev, ns, +1, reinterpret_cast<uint16_t*>(host.data() + tc_off + tcf));
+        fill_tc_steps(fwd, ns, -1, reinterpret_cast<float2*>(host.data() + tc_off + tcf));
+        fill_tc_steps(rev, ns, -1, reinterpret_cast<float2*>(host.data() + tc_off + tcf + tsf));
     }
     auto rec = std::make_unique<PlanRec>();
     rec->k = k;
@@ -290,10 +319,7 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
         rec->fwd.p[s] = s < ns ? rec->tw + of[s] : nullptr;
         rec->rev.p[s] = s < ns ? rec->tw + orv[s] : nullptr;
     }
-    if (k->tc_smem > 0) {
-        rec->tc_fwd = reinterpret_cast<const uint16_t*>(static_cast<char*>(d) + tc_off);
-        rec->tc_inv = reinterpret_cast<const uint16_t*>(static_cast<char*>(d) + tc_off + tcf);
-    }
+    if (k->tc_smem > 0) rec->tc_tables = static_cast<char*>(d) + tc_off;
     *out = rec.get();
     ctx->plans.emplace(N, std::move(rec));
     return LP_OK;
@@ -697,8 +723,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.ncols = d.ncols;
             b.twf = py->fwd;
             b.twi = py->rev;
-            a2.mats_fwd = py->tc_fwd;
-            a2.mats_inv = py->tc_inv;
+            a2.tables = static_cast<const uint4*>(py->tc_tables);
             a2.err = ctx->d_err;
             const int tok = lp_pass_begin(ctx, 1, st);
             CUDA_TRY(py->k->p2tc(a2, spectra[base + i]->is_real != 0, st));

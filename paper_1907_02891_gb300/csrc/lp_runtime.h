@@ -26,10 +26,10 @@ struct PlanRec {
     float2* tw = nullptr;  // device twiddle tables (forward chain, then reversed chain)
     size_t bytes = 0;
     lpk::TwChain fwd{}, rev{};
-    // split-BF16 DFT matrices of the tensor-core column pass (same block as
-    // tw; null where the length has no such pass)
-    const uint16_t* tc_fwd = nullptr;
-    const uint16_t* tc_inv = nullptr;
+    // tables of the tensor-core column pass (split-BF16 DFT matrices, then
+    // twiddle step factors; same block as tw; null where the length has no
+    // such pass)
+    const void* tc_tables = nullptr;
 };
 
 struct Workspace {

@@ -16,7 +16,9 @@
 // stage's twiddle and splitting it into hi/lo -- so no FP32 exchange buffer
 // is needed.  Between the forward and the inverse column transform the
 // outputs are multiplied by the PSF spectrum; after the inverse, the kept
-// rows are stored to U.  The row passes P1 and P3 stay in FP32.
+// rows are stored to U.  The inverse runs as conj(DFT(conj(x))), so both
+// chains use the forward matrices and twiddle signs.  The row passes P1 and
+// P3 stay in FP32.
 //
 // Shared-memory operand layout (the canonical "no swizzle, K-major" form):
 // 8 x 16-byte core matrices, core (row group g, k group kg) at byte
@@ -34,13 +36,16 @@ namespace lpk {
 
 constexpr int ru16(int x) { return (x + 15) / 16 * 16; }
 
-// DFT matrices of the forward chain and of the reversed (inverse) chain:
-// per stage, hi then lo, each Kp x Kp bf16 in the core-matrix layout (rows =
-// outputs n, columns = inputs k, zero padded), stages one after another.
+// Tables of the pass, one contiguous device block copied to shared memory
+// by every block: the forward DFT matrices of the forward chain's stages --
+// per stage hi then lo, each Kp x Kp bf16 in the core-matrix layout (rows =
+// outputs n, columns = inputs k, zero padded) -- then the twiddle step
+// factors of the forward and of the reversed chain: per stage s >= 1,
+// exp(-i 2 pi m k / (R_{s-1} R_s)) at [m R_{s-1} + k], m < R_s, k < R_{s-1}.
+// The inverse transform runs as conj(DFT(conj(x))) on the same matrices.
 struct P2TcArgs {
     P2Args a;  // as the FP32 column pass, one spectrum (a.K[0])
-    const uint16_t* mats_fwd;
-    const uint16_t* mats_inv;
+    const uint4* tables;
     int* err;  // device status word (bit 2: an MMA wait timed out)
 };
 
@@ -103,12 +108,28 @@ template <int N, int... Rs> struct TcChainInfo<N, Seq<Rs...>> {
         }
         return m;
     }
-    static constexpr int mat_bytes()
+    // bytes of the matrices of stages [0, upto)
+    static constexpr int mat_bytes(int upto = S)
     {
         const int rs[] = {Rs...};
         int t = 0;
-        for (int s = 0; s < S; ++s) t += 2 * ru16(2 * rs[s]) * ru16(2 * rs[s]) * 2;
+        for (int s = 0; s < upto; ++s) t += 2 * ru16(2 * rs[s]) * ru16(2 * rs[s]) * 2;
         return t;
+    }
+    // bytes of the step factors of stages [1, upto)
+    static constexpr int step_bytes_upto(int upto)
+    {
+        const int rs[] = {Rs...};
+        int b = 0;
+        for (int s = 1; s < upto; ++s) b += rs[s - 1] * rs[s] * 8;
+        return b;
+    }
+    static constexpr int step_bytes()
+    {
+        const int rs[] = {Rs...};
+        int b = 0;
+        for (int s = 1; s < S; ++s) b += rs[s - 1] * rs[s] * 8;
+        return b;
     }
     static constexpr int tmem_cols()
     {
@@ -136,13 +157,32 @@ template <class P, int N>
 struct TcPlan {
     using FI = TcChainInfo<N, typename P::Fwd>;
     using II = TcChainInfo<N, typename P::Inv>;
+    static constexpr int S = FI::S;
     static constexpr int A_BYTES = FI::a_bytes();   // the inverse has the same radices
-    static constexpr int MATF_BYTES = FI::mat_bytes();
-    static constexpr int MAT_BYTES = MATF_BYTES + II::mat_bytes();
+    // one matrix per forward stage: the inverse chain runs in the conjugate
+    // domain on the same (forward) matrices
+    static constexpr int MAT_BYTES = FI::mat_bytes();
+    static constexpr int STEPF_BYTES = FI::step_bytes();
+    static constexpr int TAB_BYTES = (MAT_BYTES + STEPF_BYTES + II::step_bytes() + 15) / 16 * 16;
     static constexpr int TMEM_COLS = FI::tmem_cols();
-    static constexpr int SMEM_BYTES = A_BYTES + MAT_BYTES + 64;
+    static constexpr int SMEM_BYTES = A_BYTES + TAB_BYTES + 64;
     static constexpr int THREADS = tc_threads<P, N>();
     static constexpr bool FITS = TMEM_COLS <= 512 && SMEM_BYTES <= 227 * 1024 && THREADS <= 1024;
+    // resident blocks per SM the shared memory allows (1..3): the register
+    // budget of the launch bounds
+    static constexpr int BY_SMEM = (228 * 1024) / (SMEM_BYTES + 1024);
+    static constexpr int MINB = BY_SMEM < 1 ? 1 : (BY_SMEM > 3 ? 3 : BY_SMEM);
+    // shared-memory layout of the stages: matrix byte offset (from the
+    // matrices' base) and step-factor byte offset (from the dynamic shared
+    // memory's base); inverse stage s uses forward stage S-1-s's matrix
+    struct FwdLayout {
+        static constexpr int moff(int s) { return FI::mat_bytes(s); }
+        static constexpr int soff(int s) { return A_BYTES + MAT_BYTES + FI::step_bytes_upto(s + 1); }
+    };
+    struct InvLayout {
+        static constexpr int moff(int s) { return FI::mat_bytes(S - 1 - s); }
+        static constexpr int soff(int s) { return A_BYTES + MAT_BYTES + STEPF_BYTES + II::step_bytes_upto(s + 1); }
+    };
 };
 
 // Issue the split-precision MMAs of one stage (one thread) and commit them
@@ -258,10 +298,10 @@ struct TcState {
 // MMA completed.  Outputs are consumed 8 at a time as they leave TMEM;
 // `sink.pad()` runs first, after the last MMA wait (the sink's own writes
 // of the A operand start there).
-template <int N, int DIR, int Ns, int SIdx, int MOFF, class S> struct TcChain;
+template <int N, int Ns, int SIdx, class LO, class S> struct TcChain;
 
-template <int N, int DIR, int Ns, int SIdx, int MOFF, int R, int... Rest>
-struct TcChain<N, DIR, Ns, SIdx, MOFF, Seq<R, Rest...>> {
+template <int N, int Ns, int SIdx, class LO, int R, int... Rest>
+struct TcChain<N, Ns, SIdx, LO, Seq<R, Rest...>> {
     using G = TcStage<N, R, Ns>;
 
     // issue this stage's MMAs and wait for them; false if the block is dead
@@ -273,7 +313,7 @@ struct TcChain<N, DIR, Ns, SIdx, MOFF, Seq<R, Rest...>> {
         const bool dead = *st.dead != 0;
         if (!dead && threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            tc_issue<G>(st.tbase, sm_u32(tc_dsmem), st.bsm + MOFF, st.mbar);
+            tc_issue<G>(st.tbase, sm_u32(tc_dsmem), st.bsm + LO::moff(SIdx), st.mbar);
         }
         bool ok = dead ? false : tc_wait(st.mbar, st.phase);
         st.phase ^= 1u;
@@ -287,8 +327,9 @@ struct TcChain<N, DIR, Ns, SIdx, MOFF, Seq<R, Rest...>> {
     template <class Sink>
     __device__ __forceinline__ static void run(TcState& st, const TwChain& tw, int* err, int t, Sink& sink)
     {
-        const bool ok = mma(st, err);
         if constexpr (sizeof...(Rest) == 0) {
+            sink.prefetch();  // global loads of the sink overlap the last MMA
+            const bool ok = mma(st, err);
             sink.pad();
             if (ok) {
 #pragma unroll
@@ -308,19 +349,23 @@ struct TcChain<N, DIR, Ns, SIdx, MOFF, Seq<R, Rest...>> {
             // Stockham placement: output k of butterfly t goes to
             // p = (t / Ns) P + t mod Ns + k Ns (P = Ns R).  The next stage's
             // butterfly count NB2 is a multiple of P, so its slot m2 = p / NB2
-            // is the same for every k, its butterfly is j2 = j20 + k Ns, and
-            // its twiddle index is (m2 - 1) P + p mod P.
+            // is the same for every k and its butterfly is j2 = j20 + k Ns.
+            // Its twiddle exp(-i 2 pi m2 (t mod Ns + k Ns) / (P R2)) is w0
+            // (the table entry of k = 0, loaded before the MMA wait) times
+            // the step factor exp(-i 2 pi m2 k / (R R2)) (shared table).
             constexpr int P = Ns * R;
             static_assert(G2::NB % P == 0, "next stage's butterfly count must be a multiple of the group size");
+            const int base = (t / Ns) * P + (t % Ns);
+            const int m2 = base / G2::NB;
+            const int j20 = base - m2 * G2::NB;
+            const float2* tab = tw.p[SIdx + 1];
+            asm volatile("" : "+l"(tab));  // no hoisting above the previous stage's wait
+            float2 w0 = make_float2(1.f, 0.f);
+            if (m2 > 0 && t < G::NB) w0 = __ldg(tab + (m2 - 1) * P + (t % Ns));
+            const bool ok = mma(st, err);
             if (t < G2::NB) tc_zero_pad<G2>(t);
             if (ok) {
-                const int base = (t / Ns) * P + (t % Ns);
-                const int m2 = base / G2::NB;
-                const int j20 = base - m2 * G2::NB;
-                const float2* tab = tw.p[SIdx + 1] + (m2 - 1) * P + (t % Ns);
-                // opaque after the MMA wait: read-only loads may otherwise be
-                // hoisted above it, keeping every stage's twiddles live at once
-                asm volatile("" : "+l"(tab));
+                const float2* step = reinterpret_cast<const float2*>(tc_dsmem + LO::soff(SIdx)) + m2 * R;
 #pragma unroll
                 for (int c0 = 0; c0 < G::KP; c0 += 16) {
                     float2 y[8];
@@ -331,17 +376,13 @@ struct TcChain<N, DIR, Ns, SIdx, MOFF, Seq<R, Rest...>> {
                             const int k = c0 / 2 + i;
                             if (k >= R) continue;
                             float2 z = y[i];
-                            if (m2 > 0) {
-                                float2 w = __ldg(tab + k * Ns);
-                                if constexpr (DIR > 0) w.y = -w.y;
-                                z = cmul(z, w);
-                            }
+                            if (m2 > 0) z = cmul(z, cmul(w0, step[k]));
                             tc_put<G2>(j20 + k * Ns, m2, z);
                         }
                     }
                 }
             }
-            TcChain<N, DIR, Ns * R, SIdx + 1, MOFF + G::MAT_BYTES, Seq<Rest...>>::run(st, tw, err, t, sink);
+            TcChain<N, Ns * R, SIdx + 1, LO, Seq<Rest...>>::run(st, tw, err, t, sink);
         }
     }
 };
@@ -354,24 +395,32 @@ template <int N, int RL, bool KREAL, class GI0>
 struct TcProductSink {
     const void* kcol;  // spectrum column c
     int t;
-    // runs after the forward chain's last MMA wait; the spectrum pointer
-    // becomes opaque there, so its read-only loads are not hoisted above the
-    // waits
-    __device__ __forceinline__ void pad()
+    typename std::conditional<KREAL, float, float2>::type kv[RL];
+    // before the forward chain's last MMA wait: the spectrum values of this
+    // thread's frequencies (the pointer becomes opaque here, so the loads are
+    // not hoisted further up)
+    __device__ __forceinline__ void prefetch()
     {
         asm volatile("" : "+l"(kcol));
+        if (t < N / RL) {
+#pragma unroll
+            for (int k = 0; k < RL; ++k) {
+                const int f = t + k * (N / RL);
+                if constexpr (KREAL) kv[k] = __ldg(static_cast<const float*>(kcol) + f);
+                else kv[k] = __ldg(static_cast<const float2*>(kcol) + f);
+            }
+        }
+    }
+    // after the last MMA wait: the A operand now takes the inverse's inputs
+    __device__ __forceinline__ void pad()
+    {
         if (t < GI0::NB) tc_zero_pad<GI0>(t);
     }
     __device__ __forceinline__ void operator()(int k, float2 z) const
     {
-        const int f = t + k * (N / RL);
-        if constexpr (KREAL) {
-            const float kv = __ldg(static_cast<const float*>(kcol) + f);
-            z = make_float2(z.x * kv, z.y * kv);
-        } else {
-            z = cmul(z, __ldg(static_cast<const float2*>(kcol) + f));
-        }
-        tc_put<GI0>(t, k, z);
+        if constexpr (KREAL) z = make_float2(z.x * kv[k], z.y * kv[k]);
+        else z = cmul(z, kv[k]);
+        tc_put<GI0>(t, k, make_float2(z.x, -z.y));  // the inverse runs on conjugates
     }
 };
 
@@ -380,12 +429,13 @@ template <int N, int R0>
 struct TcStoreSink {
     float2* Uc;
     int r0, Hout, t;
-    __device__ __forceinline__ void pad() const {}
+    __device__ __forceinline__ void prefetch() {}
+    __device__ __forceinline__ void pad() {}
     __device__ __forceinline__ void operator()(int k, float2 z) const
     {
         int rr = t + k * (N / R0) - r0;
         if (rr < 0) rr += N;
-        if (rr < Hout) Uc[rr] = z;
+        if (rr < Hout) Uc[rr] = make_float2(z.x, -z.y);  // back from the conjugate domain
     }
 };
 
@@ -401,8 +451,11 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
     using TP = TcPlan<P, N>;
     using G0 = TcStage<N, R0, 1>;   // first forward stage
     using GI0 = TcStage<N, RL, 1>;  // first inverse stage
-    using Fwd = TcChain<N, -1, 1, 0, 0, typename P::Fwd>;
-    using Inv = TcChain<N, +1, 1, 0, TP::MATF_BYTES, typename P::Inv>;
+    using Fwd = TcChain<N, 1, 0, typename TP::FwdLayout, typename P::Fwd>;
+    // the inverse transform as conj(DFT(conj(x))): the same forward matrices,
+    // step factors and twiddle signs; the product sink stores conjugates and
+    // the store sink conjugates back
+    using Inv = TcChain<N, 1, 0, typename TP::InvLayout, typename P::Inv>;
     const P2Args& a = A.a;
     const int t = threadIdx.x;
     __syncthreads();  // the previous column's last writes of As are consumed
@@ -429,24 +482,20 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
 
 // The column pass: persistent blocks, one column of one spectrum at a time.
 template <class P, int N, bool KREAL>
-__global__ void __launch_bounds__(tc_threads<P, N>(), tc_threads<P, N>() <= 512 ? 2 : 1) p2_cols_tc(const __grid_constant__ P2TcArgs A)
+__global__ void __launch_bounds__(TcPlan<P, N>::THREADS, TcPlan<P, N>::MINB) p2_cols_tc(const __grid_constant__ P2TcArgs A)
 {
     using TP = TcPlan<P, N>;
     const P2Args& a = A.a;
     const int t = threadIdx.x;
     unsigned char* Bs = tc_dsmem + TP::A_BYTES;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + TP::MAT_BYTES);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + TP::TAB_BYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     int* dead = reinterpret_cast<int*>(tslot + 1);
 
-    // DFT matrices (forward chain, then inverse chain) into shared memory
+    // matrices and step factors into shared memory
     {
-        const uint4* srcf = reinterpret_cast<const uint4*>(A.mats_fwd);
-        const uint4* srci = reinterpret_cast<const uint4*>(A.mats_inv);
         uint4* dst = reinterpret_cast<uint4*>(Bs);
-        for (int i = t; i < TP::MATF_BYTES / 16; i += blockDim.x) dst[i] = srcf[i];
-        for (int i = t; i < (TP::MAT_BYTES - TP::MATF_BYTES) / 16; i += blockDim.x)
-            dst[TP::MATF_BYTES / 16 + i] = srci[i];
+        for (int i = t; i < TP::TAB_BYTES / 16; i += blockDim.x) dst[i] = A.tables[i];
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm_u32(mbar)));
