@@ -38,7 +38,9 @@ FALLBACK_HBM_GBS = 6800.0
 PASSES = ("p1_rows", "p2_cols", "p3_rows")
 KERNEL_SOURCES = ("paper_1907_02891_gb300/csrc/fft_core.cuh",
                   "paper_1907_02891_gb300/csrc/conv_kernels.cuh",
-                  "paper_1907_02891_gb300/build.py")
+                  "paper_1907_02891_gb300/build.py",
+                  "paper_1907_02891_gb300/tuned_plans.json")
+TC_SOURCES = ("paper_1907_02891_gb300/csrc/tc_kernels.cuh",)
 
 
 def parse_args():
@@ -98,9 +100,9 @@ def whole_job_mpix_s(px_per_rank_per_step: float, steps: int, world: int, max_ms
     return px_per_rank_per_step * steps * world / (max_ms / 1e3) / 1e6
 
 
-def kernel_source_sha():
+def kernel_source_sha(extra=()):
     h = hashlib.sha1()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES + tuple(extra):
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -117,14 +119,16 @@ def measured_peak():
 
 
 def dram_traffic(kernel, workload):
-    """ncu dram bytes per launch, if captured for the current kernel source."""
+    """ncu dram bytes per launch, if captured for the current kernel source
+    (the tensor-core column pass, "p2_cols_tc", also fingerprints its own
+    header)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as fh:
             rec = json.load(fh)[workload][kernel]
     except Exception:
         return None
-    if rec.get("source_sha") != kernel_source_sha():
+    if rec.get("source_sha") != kernel_source_sha(TC_SOURCES if kernel.endswith("_tc") else ()):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -402,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
     per_launch_bytes = model[dom] * (args.steps / max(1, launches))
     achieved = per_launch_bytes / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    traffic = dram_traffic(dom, wl.name)
+    traffic = dram_traffic(dom + ("_tc" if prec != lp.LP_PREC_FP32 and dom == "p2_cols" else ""), wl.name)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

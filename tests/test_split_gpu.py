@@ -126,6 +126,15 @@ def test_split_map8192_psf601x16_sampled(ctx):
         assert _sampled_check(L, K, B, wl.seed + 200 + k, n=256, top=16) <= TOL_SPLIT, k
 
 
+def test_split_map16384_psf801_sampled(ctx):
+    """The 16384^2 map with the 801^2 PSF (padded 17280^2): the workload the
+    split-precision bar of 2e-4 is stated for."""
+    wl = synth.WORKLOADS["map16384_psf801"]
+    L, K = wl.radiance(), wl.psfs()[0]
+    (B,) = run_split(ctx, L, [K])
+    assert _sampled_check(L, K, B, wl.seed + 200) <= TOL_SPLIT
+
+
 def test_split_host_entry_point_matches_device(ctx):
     g = np.random.default_rng(22)
     L = g.lognormal(0.0, 1.0, (77, 117)).astype(np.float32)
