@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 PASSES = ("p1_rows", "p2_cols", "p3_rows")
 KERNEL_SOURCES = ("paper_1907_02891_gb300/csrc/fft_core.cuh",
                   "paper_1907_02891_gb300/csrc/conv_kernels.cuh",
-                  "paper_1907_02891_gb300/build.py",
-                  "paper_1907_02891_gb300/tuned_plans.json")
+                  "paper_1907_02891_gb300/build.py")
+TUNED_PLANS = "paper_1907_02891_gb300/tuned_plans.json"
 TC_SOURCES = ("paper_1907_02891_gb300/csrc/tc_kernels.cuh",)
 
 
@@ -100,11 +100,20 @@ def whole_job_mpix_s(px_per_rank_per_step: float, steps: int, world: int, max_ms
     return px_per_rank_per_step * steps * world / (max_ms / 1e3) / 1e6
 
 
-def kernel_source_sha(extra=()):
+def kernel_source_sha(extra=(), lengths=()):
+    """Fingerprint of the kernel sources and of the measured plans of the
+    given FFT lengths (the plans of other lengths do not change them)."""
     h = hashlib.sha1()
     for p in KERNEL_SOURCES + tuple(extra):
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, TUNED_PLANS)) as fh:
+            tuned = json.load(fh)
+    except (OSError, ValueError):
+        tuned = {}
+    for n in sorted(set(lengths)):
+        h.update(json.dumps(tuned.get(str(n)), sort_keys=True).encode())
     return h.hexdigest()[:16]
 
 
@@ -118,7 +127,7 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def dram_traffic(kernel, workload):
+def dram_traffic(kernel, workload, lengths):
     """ncu dram bytes per launch, if captured for the current kernel source
     (the tensor-core column pass, "p2_cols_tc", also fingerprints its own
     header)."""
@@ -128,7 +137,7 @@ def dram_traffic(kernel, workload):
             rec = json.load(fh)[workload][kernel]
     except Exception:
         return None
-    if rec.get("source_sha") != kernel_source_sha(TC_SOURCES if kernel.endswith("_tc") else ()):
+    if rec.get("source_sha") != kernel_source_sha(TC_SOURCES if kernel.endswith("_tc") else (), lengths):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -406,7 +415,8 @@ def run_ours(args, rank, world, local_rank):
     per_launch_bytes = model[dom] * (args.steps / max(1, launches))
     achieved = per_launch_bytes / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    traffic = dram_traffic(dom + ("_tc" if prec != lp.LP_PREC_FP32 and dom == "p2_cols" else ""), wl.name)
+    traffic = dram_traffic(dom + ("_tc" if prec != lp.LP_PREC_FP32 and dom == "p2_cols" else ""), wl.name,
+                           (ny, nx))
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

@@ -174,9 +174,15 @@ lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
 
 /*
  * Same as lp_map with HOST buffers: copies L to the device, runs the map,
- * copies every out[k] back, all in order on `stream` (the copies are
- * asynchronous when the host memory is pinned).  Host buffers must stay
- * valid until the stream reaches that point (lp_sync_status).
+ * copies every out[k] back (the copies are asynchronous when the host memory
+ * is pinned).  `stream` reaches the end of the call only when every out[k]
+ * is in host memory; host buffers must stay valid until then
+ * (lp_sync_status).  The downloads into out[] wait for the caller's earlier
+ * work on `stream`.  The upload of L and the passes do not: they run on the
+ * context's internal streams and wait only for the previous host map's use of
+ * the context's staging buffers and for the spectra's builds.  So L_host must
+ * hold its data when the call is made, and consecutive host maps overlap (one
+ * map's passes and upload with the previous map's download).
  */
 lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w, int ldl,
                       const lp_spectrum* const* spectra, int n, float* const* out_host, int ldo,

@@ -392,6 +392,7 @@ extern "C" void lp_destroy(lp_ctx* ctx)
     cudaDeviceSynchronize();
     for (auto& kv : ctx->spectra) {
         lp_ctx_free(ctx, kv.second->data, kv.second->bytes);
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
         delete kv.second;
     }
     ctx->spectra.clear();
@@ -408,8 +409,11 @@ extern "C" void lp_destroy(lp_ctx* ctx)
     for (auto ev : ctx->tim_pool) cudaEventDestroy(ev);
     for (auto ev : ctx->hs_events) cudaEventDestroy(ev);
     if (ctx->hs_lfree) cudaEventDestroy(ctx->hs_lfree);
+    for (auto ev : ctx->hs_ofree)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->hs_in) cudaStreamDestroy(ctx->hs_in);
     if (ctx->hs_out) cudaStreamDestroy(ctx->hs_out);
+    if (ctx->hs_comp) cudaStreamDestroy(ctx->hs_comp);
     delete ctx;
 }
 
@@ -531,9 +535,12 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
                            (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
                            (double2*)(scratch + 2 * w1 + w2), st);
     cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&spec->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(spec->ready, st);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(st);
         lp_ctx_free(ctx, dptr, bytes);
+        if (spec->ready) cudaEventDestroy(spec->ready);
         delete spec;
         return lp_fail(LP_ERR_CUDA, "spectrum build: %s", cudaGetErrorString(e));
     }
@@ -545,6 +552,7 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
             *out = it->second;
             cudaStreamSynchronize(st);
             lp_ctx_free(ctx, dptr, bytes);
+            cudaEventDestroy(spec->ready);
             delete spec;
             return LP_OK;
         }
@@ -593,6 +601,7 @@ extern "C" lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s)
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();  // in-flight maps may still read it
         lp_ctx_free(ctx, s->data, s->bytes);
+        if (s->ready) cudaEventDestroy(s->ready);
         ctx->spectra.erase(it);
         delete s;
     }
@@ -845,6 +854,8 @@ static lp_status host_streams(lp_ctx* ctx)
     if (ctx->hs_in) return LP_OK;
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hs_in, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hs_out, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hs_comp, cudaStreamNonBlocking));
+    for (auto& ev : ctx->hs_ofree) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     for (int i = 0; i < 2 * kHostBands + 2; ++i) {
         cudaEvent_t e;
         CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -869,11 +880,13 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     const PlanRec *py, *px;
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
     if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
-    // staging: L (h x w, packed) then n outputs (Hout x Wout, packed)
+    // staging: L (h x w, packed), then two sets of n outputs (Hout x Wout,
+    // packed) that alternate between calls
     const size_t lbytes = 4ull * (size_t)h * w;
     const size_t obytes = 4ull * (size_t)d.Hout * d.Wout;
-    const size_t need = ((lbytes + 255) / 256 * 256) + (size_t)n * ((obytes + 255) / 256 * 256);
-    std::lock_guard<std::mutex> host_lock(ctx->host_mu);  // one host map in flight per context
+    const size_t lb = (lbytes + 255) / 256 * 256, ob = (obytes + 255) / 256 * 256;
+    const size_t need = lb + 2ull * (size_t)n * ob;
+    std::lock_guard<std::mutex> host_lock(ctx->host_mu);  // one host map enqueued at a time per context
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
         if (ctx->staging_bytes < need) {
@@ -889,19 +902,18 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
             ctx->staging = p;
             ctx->staging_bytes = need;
             ctx->hs_lfree_valid = false;
+            ctx->hs_ofree_valid[0] = ctx->hs_ofree_valid[1] = false;
         }
     }
     if ((st = host_streams(ctx)) != LP_OK) return st;
+    cudaStream_t c = ctx->hs_comp;  // the passes of host maps run here, with their own workspace
+    const int obuf = ctx->hs_obuf;
     char* base = static_cast<char*>(ctx->staging);
     float* dL = reinterpret_cast<float*>(base);
     std::vector<float*> dout(n);
-    char* p = base + (lbytes + 255) / 256 * 256;
-    for (int k = 0; k < n; ++k) {
-        dout[k] = reinterpret_cast<float*>(p);
-        p += (obytes + 255) / 256 * 256;
-    }
+    for (int k = 0; k < n; ++k) dout[k] = reinterpret_cast<float*>(base + lb + ((size_t)obuf * n + k) * ob);
     void* ws = nullptr;
-    st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
+    st = lp_get_workspace(ctx, c, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
     float2* T = static_cast<float2*>(ws);
     float2* U = T + (size_t)d.ncols * d.ldT;
@@ -911,15 +923,20 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     cudaEvent_t* ev_out = ev + 2 + kHostBands;   // kHostBands
     cudaEvent_t ev_lfree = ctx->hs_lfree;
 
-    // The upload only has to wait until the previous host map's row pass has
-    // read the staging map (so it overlaps that map's column and inverse
-    // passes and its download); the passes and the download run after the
-    // caller's earlier work on its stream, which includes the previous host
-    // map's download.
+    // Ordering.  The upload waits until the previous host map's row pass has
+    // read the staging map (the first time: for the caller's earlier work on
+    // the stream).  The passes wait only for their input bands, the spectra's
+    // builds, and -- before writing output staging buffer b -- the download
+    // of the call two back that used b; so a map's passes overlap the
+    // previous map's download.  The download waits for the caller's earlier
+    // work on the stream (it writes caller memory), and the caller's stream
+    // waits for the download, so the stream reaches the end of this call only
+    // with every output in host memory.
     CUDA_TRY(cudaEventRecord(ev_start, s));
     if (ctx->hs_lfree_valid) CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_lfree, 0));
     else CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_start, 0));
     CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_start, 0));
+    for (int k = 0; k < n; ++k) CUDA_TRY(cudaStreamWaitEvent(c, spectra[k]->ready, 0));
 
     const int npairs = (int)(d.ldT / 2);
     const int nb_in = npairs < kHostBands ? npairs : kHostBands;
@@ -930,21 +947,22 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
             CUDA_TRY(cudaMemcpy2DAsync(dL + (size_t)r0 * w, 4ull * w, L_host + (size_t)r0 * ldl, 4ull * ldl,
                                        4ull * w, r1 - r0, cudaMemcpyHostToDevice, ctx->hs_in));
         CUDA_TRY(cudaEventRecord(ev_in[b], ctx->hs_in));
-        CUDA_TRY(cudaStreamWaitEvent(s, ev_in[b], 0));
-        if ((st = launch_rows_forward(ctx, px, dL, h, w, w, d, T, q0, q1, s)) != LP_OK) return st;
+        CUDA_TRY(cudaStreamWaitEvent(c, ev_in[b], 0));
+        if ((st = launch_rows_forward(ctx, px, dL, h, w, w, d, T, q0, q1, c)) != LP_OK) return st;
     }
-    CUDA_TRY(cudaEventRecord(ev_lfree, s));  // the staging map may be overwritten after this
+    CUDA_TRY(cudaEventRecord(ev_lfree, c));  // the staging map may be overwritten after this
     ctx->hs_lfree_valid = true;
     const int opairs = (int)(d.ldU / 2);
     const int nb_out = opairs < kHostBands ? opairs : kHostBands;
     for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {
         const int cnt = (n - cb) < kMaxSpectraPerLaunch ? (n - cb) : kMaxSpectraPerLaunch;
-        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, s)) != LP_OK) return st;
+        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, c)) != LP_OK) return st;
+        if (cb == 0 && ctx->hs_ofree_valid[obuf]) CUDA_TRY(cudaStreamWaitEvent(c, ctx->hs_ofree[obuf], 0));
         for (int b = 0; b < nb_out; ++b) {
             const int q0 = (int)((long long)opairs * b / nb_out), q1 = (int)((long long)opairs * (b + 1) / nb_out);
-            if ((st = launch_rows_inverse(ctx, px, d, U, cnt, dout.data() + cb, d.Wout, q0, q1, s)) != LP_OK)
+            if ((st = launch_rows_inverse(ctx, px, d, U, cnt, dout.data() + cb, d.Wout, q0, q1, c)) != LP_OK)
                 return st;
-            CUDA_TRY(cudaEventRecord(ev_out[b], s));
+            CUDA_TRY(cudaEventRecord(ev_out[b], c));
             CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_out[b], 0));
             const int r0 = 2 * q0, r1 = (2 * q1 < d.Hout) ? 2 * q1 : d.Hout;
             if (r1 <= r0) continue;
@@ -953,12 +971,10 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
                                            4ull * d.Wout, 4ull * d.Wout, r1 - r0, cudaMemcpyDeviceToHost,
                                            ctx->hs_out));
         }
-        if (cb + cnt < n) {
-            // the next chunk's inverse row pass overwrites U: wait for these copies
-            CUDA_TRY(cudaEventRecord(ev_end, ctx->hs_out));
-            CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
-        }
     }
+    CUDA_TRY(cudaEventRecord(ctx->hs_ofree[obuf], ctx->hs_out));
+    ctx->hs_ofree_valid[obuf] = true;
+    ctx->hs_obuf = obuf ^ 1;
     CUDA_TRY(cudaEventRecord(ev_end, ctx->hs_out));
     CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
     return LP_OK;

@@ -62,6 +62,7 @@ struct lp_spectrum {
     size_t bytes = 0;
     int refcount = 0;
     void* data = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded after the build on the building stream
 };
 
 struct lp_ctx {
@@ -82,10 +83,13 @@ struct lp_ctx {
     std::vector<cudaEvent_t> tim_pool;
     // pipelined host-buffer map
     std::mutex host_mu;
-    cudaStream_t hs_in = nullptr, hs_out = nullptr;
+    cudaStream_t hs_in = nullptr, hs_out = nullptr, hs_comp = nullptr;
     std::vector<cudaEvent_t> hs_events;
     cudaEvent_t hs_lfree = nullptr;  // previous host map's row pass done with the staging map
     bool hs_lfree_valid = false;
+    cudaEvent_t hs_ofree[2] = {nullptr, nullptr};  // download from output staging b done
+    bool hs_ofree_valid[2] = {false, false};
+    int hs_obuf = 0;  // output staging buffer of the next host map
 };
 
 lp_status lp_fail(lp_status st, const char* fmt, ...);

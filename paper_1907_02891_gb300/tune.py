@@ -34,6 +34,13 @@ TUNED_JSON = os.path.join(B.HERE, "tuned_plans.json")
 COMMON_SRCS = ("api.cu", "spectrum.cu", "noalloc.cu", "serve.cpp")
 
 
+def _prod(p) -> int:
+    r = 1
+    for x in p:
+        r *= x
+    return r
+
+
 def candidate_plans(n: int, limit: int = 3) -> List[Tuple[int, ...]]:
     """Radix sequences ordered like build.choose_plan, then the other orders
     of the same multisets (first radix odd / large first)."""
@@ -110,26 +117,26 @@ import torch
 sys.path.insert(0, {root!r})
 import paper_1907_02891_gb300.lp as lp
 lp.load_library({lib!r})
-n, reps, side = {n}, {reps}, {side}
-hk = min(541, max(3, (n // 8) | 1))
+n, reps, side, psf, nspec = {n}, {reps}, {side}, {psf}, {nspec}
+hk = psf if psf > 0 else min(541, max(3, (n // 8) | 1))
 h = w = side if side > 0 else n - hk + 1
 dev = torch.device("cuda", 0)
 ctx = lp.lp_create(0)
 g = np.random.default_rng(1)
 L = torch.from_numpy(g.random((h, w), dtype=np.float32)).to(dev)
 r = np.hypot(*np.meshgrid(np.arange(hk) - hk // 2, np.arange(hk) - hk // 2, indexing="ij"))
-K = torch.from_numpy((r * r + 0.1) ** -1.25).to(dev)
-s = lp.lp_kernel_spectrum(ctx, K, pad_ny=n, pad_nx=n)
-out = torch.empty_like(L)
+specs = [lp.lp_kernel_spectrum(ctx, torch.from_numpy((r * r + 0.1) ** -(1.0 + 0.25 * i)).to(dev),
+                               pad_ny=n, pad_nx=n) for i in range(nspec)]
+outs = [torch.empty_like(L) for _ in specs]
 flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 for _ in range(5):
-    lp.lp_map(ctx, L, [s], [out])
+    lp.lp_map(ctx, L, specs, outs)
 lp.lp_sync_status(ctx)
 lp.lp_set_pass_timing(ctx, True)
 lp.lp_get_pass_timing(ctx)
 for _ in range(reps):
     flush.zero_()
-    lp.lp_map(ctx, L, [s], [out])
+    lp.lp_map(ctx, L, specs, outs)
 lp.lp_sync_status(ctx)
 t = lp.lp_get_pass_timing(ctx)
 print(json.dumps({{k: v[0] / max(1, v[1]) for k, v in t.items()}}))
@@ -137,17 +144,18 @@ lp.lp_destroy(ctx)
 """
 
 
-def time_variant(lib: str, n: int, reps: int, side: int = 0) -> Dict[str, float]:
-    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps, side=side)
+def time_variant(lib: str, n: int, reps: int, side: int = 0, psf: int = 0, nspec: int = 1) -> Dict[str, float]:
+    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps, side=side, psf=psf, nspec=nspec)
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     if res.returncode != 0:
         raise RuntimeError(f"timing failed for {lib}:\n{res.stderr[-2000:]}")
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int = 0) -> dict:
+def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int = 0, psf: int = 0,
+              nspec: int = 1, plans: List[Tuple[int, ...]] = ()) -> dict:
     base = B.plan_table_entry(n)
-    plans = candidate_plans(n, 2 if quick else 3)
+    plans = list(plans) or candidate_plans(n, 2 if quick else 3)
     knobs = []
     for upb, minb, kst in itertools.product((1, 2, 3), (1, 2, 3), (False, True)):
         if quick and (minb == 3 and upb == 1):
@@ -181,7 +189,7 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
     results = []
     for p, lib in zip(variants, libs):
         try:
-            t = time_variant(lib, n, 200 if n <= 5200 else 40, side)
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
         except Exception as e:  # a variant that does not launch (resources) is skipped
             log(f"  skip {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={p['kstage']}: "
                 f"{str(e).splitlines()[-1][:120]}")
@@ -230,7 +238,7 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
     db, minb = [0, 0, 0], list(out["minb"])
     for p, lib in zip(refine, rlibs):
         try:
-            t = time_variant(lib, n, 200 if n <= 5200 else 40, side)
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
         except Exception as e:
             log(f"  skip db=1 minb={p['minb'][0]}: {str(e).splitlines()[-1][:120]}")
             continue
@@ -251,8 +259,12 @@ def main() -> None:
     ap.add_argument("--jobs", type=int, default=0)
     ap.add_argument("--out", default=TUNED_JSON)
     ap.add_argument("--log", default=None)
+    ap.add_argument("--plan", action="append", default=[],
+                    help="radix sequence to try, e.g. 7,7,8,12 (repeatable; default: the candidate list)")
+    ap.add_argument("--psf", type=int, default=0, help="PSF side of the timed maps (default min(541, N/8))")
+    ap.add_argument("--nspec", type=int, default=1, help="spectra per timed map (one forward transform)")
     ap.add_argument("--map-side", type=int, default=0,
-                    help="time maps of this side (PSF 541^2) instead of N - 540, to compare "
+                    help="time maps of this side instead of N - PSF + 1, to compare "
                          "padded lengths for one workload")
     args = ap.parse_args()
     jobs = args.jobs or (os.cpu_count() or 1)
@@ -267,13 +279,18 @@ def main() -> None:
     for n in args.sizes:
         if n not in B.SIZES:
             raise SystemExit(f"{n} is not in the supported size list")
+    plans = [tuple(int(x) for x in p.split(",")) for p in args.plan]
+    for p in plans:
+        if len(args.sizes) != 1 or _prod(p) != args.sizes[0] or max(p) > 32:
+            raise SystemExit(f"plan {p} is not a radix sequence of length {args.sizes}")
     common = _compile_common(jobs)
     table = {}
     if os.path.exists(args.out):
         with open(args.out) as fh:
             table = json.load(fh)
     for n in args.sizes:
-        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side)
+        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side, args.psf, args.nspec, plans)
+        table[str(n)]["tuned_on"] = {"map_side": args.map_side, "psf": args.psf, "nspec": args.nspec}
         with open(args.out, "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
     log(f"wrote {args.out}")

@@ -240,6 +240,29 @@ def test_host_entry_point_banded_ragged_full_mode(ctx):
         lp.lp_spectrum_release(ctx, s)
 
 
+def test_host_entry_point_back_to_back_calls(ctx):
+    """Consecutive host maps overlap (a map's passes with the previous map's
+    download, output staging alternating between two buffers): five calls
+    with different maps and two spectra, one sync at the end, every output
+    bitwise equal to the device path's."""
+    g = np.random.default_rng(17)
+    Ks = [synth.psf_power_exp(31, 1.0, 0.25, 1.25, 40.0), g.uniform(0.1, 1.0, (31, 31))]
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), max_h=300, max_w=280) for K in Ks]
+    Ls = [torch.from_numpy(g.lognormal(0.0, 1.0, (300, 280)).astype(np.float32)).pin_memory() for _ in range(5)]
+    outs = [[torch.full((300, 280), float("nan")).pin_memory() for _ in Ks] for _ in Ls]
+    for L, o in zip(Ls, outs):
+        lp.lp_map_host(ctx, L, specs, o)
+    lp.lp_sync_status(ctx)
+    for L, o in zip(Ls, outs):
+        ref = [torch.empty((300, 280), dtype=torch.float32, device=DEV) for _ in Ks]
+        lp.lp_map(ctx, L.to(DEV), specs, ref)
+        lp.lp_sync_status(ctx)
+        for a, b in zip(o, ref):
+            assert torch.equal(a, b.cpu())
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+
+
 # --- full-size workloads, sampled against the oracle -------------------------
 
 def _sampled_check(L, K, B, seed, n=4096, top=64):
