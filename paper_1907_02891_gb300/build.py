@@ -204,12 +204,11 @@ cudaError_t set_attrs()
 cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
     const long long sm = kX1 * kSmem + p1_stage_bytes(a.Wst);
-    if (kPF1 && sm <= kMaxSmem) {{
-        p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1><<<persistent_grid(a.npairs - a.pair0, kUPB1), P::T, sm, s>>>(a);
-    }} else {{
-        p1_rows<P, kN, kF1><<<(a.npairs - a.pair0 + kF1 - 1) / kF1, P::T * kF1, kF1 * kSmem, s>>>(a);
-    }}
-    return cudaGetLastError();
+    if (kPF1 && sm <= kMaxSmem)
+        return launch_pdl(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, dim3(persistent_grid(a.npairs - a.pair0, kUPB1)),
+                          dim3(P::T), sm, s, a);
+    return launch_pdl(p1_rows<P, kN, kF1>, dim3((a.npairs - a.pair0 + kF1 - 1) / kF1), dim3(P::T * kF1),
+                      kF1 * kSmem, s, a);
 }}
 
 cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
@@ -217,21 +216,16 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
     const bool multi = a.nspec > 1;
     const long long sm = kX2 * kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal, kKSTAGE);
     if (!multi) {{
-        if (kPF2 && sm <= kMaxSmem) {{
-            if (kreal)
-                p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
-            else
-                p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2><<<persistent_grid(a.ncols, kUPB2), P::T, sm, s>>>(a);
-        }} else {{
-            if (kreal) p2_cols<P, kN, true, false, kMINB2, kDB2><<<a.ncols, P::T, kX2 * kSmem, s>>>(a);
-            else p2_cols<P, kN, false, false, kMINB2, kDB2><<<a.ncols, P::T, kX2 * kSmem, s>>>(a);
-        }}
-        return cudaGetLastError();
+        const dim3 gpf(persistent_grid(a.ncols, kUPB2));
+        if (kPF2 && sm <= kMaxSmem)
+            return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a)
+                         : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a);
+        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a);
     }}
     if constexpr (kSmem2 <= kMaxSmem) {{
-        if (kreal) p2_cols<P, kN, true, true><<<a.ncols, P::T, kSmem2, s>>>(a);
-        else p2_cols<P, kN, false, true><<<a.ncols, P::T, kSmem2, s>>>(a);
-        return cudaGetLastError();
+        return kreal ? launch_pdl(p2_cols<P, kN, true, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
     }} else {{
         // no room to park the forward column: one pass per spectrum
         for (int i = 0; i < a.nspec; ++i) {{
@@ -249,9 +243,8 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 {{
     if constexpr (kSmem2 <= kMaxSmem) {{
-        if (kreal) p2_multiclass<P, kN, true><<<a.ncols, P::T, kSmem2, s>>>(a);
-        else p2_multiclass<P, kN, false><<<a.ncols, P::T, kSmem2, s>>>(a);
-        return cudaGetLastError();
+        return kreal ? launch_pdl(p2_multiclass<P, kN, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
+                     : launch_pdl(p2_multiclass<P, kN, false>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
     }} else {{
         return cudaErrorNotSupported;
     }}
@@ -287,9 +280,8 @@ int tc_grid(int ncols)
 cudaError_t p2tc(const P2TcArgs& a, bool kreal, cudaStream_t s)
 {{
     if constexpr (kTC) {{
-        if (kreal) p2_cols_tc<P, kN, true><<<tc_grid<true>(a.a.ncols), TP::THREADS, kTcSmem, s>>>(a);
-        else p2_cols_tc<P, kN, false><<<tc_grid<false>(a.a.ncols), TP::THREADS, kTcSmem, s>>>(a);
-        return cudaGetLastError();
+        return kreal ? launch_pdl(p2_cols_tc<P, kN, true>, dim3(tc_grid<true>(a.a.ncols)), dim3(TP::THREADS), kTcSmem, s, a)
+                     : launch_pdl(p2_cols_tc<P, kN, false>, dim3(tc_grid<false>(a.a.ncols)), dim3(TP::THREADS), kTcSmem, s, a);
     }} else {{
         return cudaErrorNotSupported;
     }}
@@ -298,12 +290,11 @@ cudaError_t p2tc(const P2TcArgs& a, bool kreal, cudaStream_t s)
 cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 {{
     const long long sm = kX3 * kSmem + p3_stage_bytes(a.ncols);
-    if (kPF3 && sm <= kMaxSmem) {{
-        p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3><<<dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec), P::T, sm, s>>>(a);
-    }} else {{
-        p3_rows<P, kN, kF3><<<dim3((a.npairs - a.pair0 + kF3 - 1) / kF3, nspec), P::T * kF3, kF3 * kSmem, s>>>(a);
-    }}
-    return cudaGetLastError();
+    if (kPF3 && sm <= kMaxSmem)
+        return launch_pdl(p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3>, dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec),
+                          dim3(P::T), sm, s, a);
+    return launch_pdl(p3_rows<P, kN, kF3>, dim3((a.npairs - a.pair0 + kF3 - 1) / kF3, nspec), dim3(P::T * kF3),
+                      kF3 * kSmem, s, a);
 }}
 }}  // namespace
 

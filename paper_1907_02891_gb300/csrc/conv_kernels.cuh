@@ -108,6 +108,38 @@ struct Plan {
     static constexpr int EJ = Chain<N, +1, N / R0, 0, T, Seq<R0>>::E;  // inverse last stage
 };
 
+// Programmatic dependent launch.  The pass kernels are launched with the
+// programmatic-stream-serialization attribute and begin with pdl_begin():
+// the trigger lets the next kernel on the stream start launching once every
+// block of this grid has started (its blocks then wait in their own
+// pdl_begin), and the wait holds this grid until the previous grid on the
+// stream has completed with its memory visible -- so no pass touches global
+// memory before its predecessor is done, while the launch latency of each
+// pass overlaps the tail of the one before.  Without the attribute (or after
+// a non-kernel operation) the wait returns at once.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // P2's spectrum product on the forward column's last-stage outputs (thread
 // t, butterfly j = t + e T holds frequencies j + m N/RL).
 template <class P, int N, bool KREAL, bool STAGED>
@@ -227,6 +259,7 @@ __device__ __forceinline__ void store_rows(const float2 (&o)[P::EJ][P::R0], int 
 template <class P, int N, int F>
 __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -290,6 +323,7 @@ __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, con
 template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2Args a)
 {
+    pdl_begin();
     static_assert(!(DB && MULTI), "the batched column pass is single-buffered");
     using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
     using Inv = typename std::conditional<DB, typename P::InvChainDB, typename P::InvChain>::type;
@@ -342,6 +376,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
 template <class P, int N, int F>
 __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int RI = P::RL, NBI = N / RI;
@@ -411,6 +446,7 @@ __host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll 
 template <class P, int N, int UPB, int MINB, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -473,6 +509,7 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -540,6 +577,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 template <class P, int N, int UPB, int MINB, bool DB = false>
 __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int RI = P::RL, NBI = N / RI;
@@ -649,6 +687,7 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
 template <class P, int N, bool KREAL>
 __global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2MArgs a)
 {
+    pdl_begin();
     extern __shared__ float2 smem2[];
     constexpr int RL = P::RL, NBL = N / RL;
     float2* sm = smem2;

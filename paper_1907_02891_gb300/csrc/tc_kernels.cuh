@@ -168,10 +168,13 @@ struct TcPlan {
     static constexpr int SMEM_BYTES = A_BYTES + TAB_BYTES + 64;
     static constexpr int THREADS = tc_threads<P, N>();
     static constexpr bool FITS = TMEM_COLS <= 512 && SMEM_BYTES <= 227 * 1024 && THREADS <= 1024;
-    // resident blocks per SM the shared memory allows (1..3): the register
-    // budget of the launch bounds
+    // resident blocks per SM for the launch bounds' register budget: what
+    // the shared memory allows, at most 3, and no more than leaves 56
+    // registers per thread
     static constexpr int BY_SMEM = (228 * 1024) / (SMEM_BYTES + 1024);
-    static constexpr int MINB = BY_SMEM < 1 ? 1 : (BY_SMEM > 3 ? 3 : BY_SMEM);
+    static constexpr int BY_REGS = 65536 / (THREADS * 56);
+    static constexpr int MINB_ = BY_SMEM < BY_REGS ? BY_SMEM : BY_REGS;
+    static constexpr int MINB = MINB_ < 1 ? 1 : (MINB_ > 3 ? 3 : MINB_);
     // shared-memory layout of the stages: matrix byte offset (from the
     // matrices' base) and step-factor byte offset (from the dynamic shared
     // memory's base); inverse stage s uses forward stage S-1-s's matrix
@@ -484,6 +487,7 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
 template <class P, int N, bool KREAL>
 __global__ void __launch_bounds__(TcPlan<P, N>::THREADS, TcPlan<P, N>::MINB) p2_cols_tc(const __grid_constant__ P2TcArgs A)
 {
+    pdl_begin();
     using TP = TcPlan<P, N>;
     const P2Args& a = A.a;
     const int t = threadIdx.x;
