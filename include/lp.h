@@ -241,6 +241,17 @@ size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int 
 lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
 
 /*
+ * Test hooks (no counterpart in the paper; for the failure-detection tests).
+ * LP_TEST_TC_NO_MMA: the split-precision column pass issues no tensor-core
+ * instruction, so its first bounded MMA wait (100 ms of device time) runs
+ * out; the kernel then sets bit 2 of the device status word, frees its
+ * tensor memory and returns, and lp_sync_status reports LP_ERR_DEVICE.  The
+ * context stays usable.  0 clears the hooks; unknown bits: LP_ERR_INVALID.
+ */
+#define LP_TEST_TC_NO_MMA 1
+lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
+
+/*
  * Serving: continuous batching of map requests.  lp_serve_start creates
  * n_slots CUDA streams (each with its own workspace) and a scheduler thread.
  * lp_serve_submit validates a request exactly like lp_map (LP_OUT_* mode,

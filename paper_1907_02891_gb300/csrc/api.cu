@@ -734,6 +734,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.twi = py->rev;
             a2.tables = static_cast<const uint4*>(py->tc_tables);
             a2.err = ctx->d_err;
+            a2.no_mma = (ctx->test_hook & LP_TEST_TC_NO_MMA) ? 1 : 0;
             const int tok = lp_pass_begin(ctx, 1, st);
             CUDA_TRY(py->k->p2tc(a2, spectra[base + i]->is_real != 0, st));
             lp_pass_end(ctx, tok, st);
@@ -977,6 +978,14 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     ctx->hs_obuf = obuf ^ 1;
     CUDA_TRY(cudaEventRecord(ev_end, ctx->hs_out));
     CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
+    return LP_OK;
+}
+
+extern "C" lp_status lp_set_test_hook(lp_ctx* ctx, int hook)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: NULL context");
+    if (hook & ~LP_TEST_TC_NO_MMA) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: unknown hook 0x%x", hook);
+    ctx->test_hook = hook;
     return LP_OK;
 }
 

@@ -75,6 +75,7 @@ struct lp_ctx {
     void* staging = nullptr;
     size_t staging_bytes = 0;
     int* d_err = nullptr;  // sticky device status word
+    int test_hook = 0;     // lp_set_test_hook
     ServeState* serve = nullptr;
     // pass timing
     std::mutex tim_mu;

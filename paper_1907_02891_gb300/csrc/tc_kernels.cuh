@@ -47,6 +47,7 @@ struct P2TcArgs {
     P2Args a;  // as the FP32 column pass, one spectrum (a.K[0])
     const uint4* tables;
     int* err;  // device status word (bit 2: an MMA wait timed out)
+    int no_mma;  // test hook: issue no MMA, so the first bounded wait runs out
 };
 
 __device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -222,16 +223,28 @@ __device__ __forceinline__ void tc_issue(uint32_t tbase, uint32_t a_smem, uint32
                  : "memory");
 }
 
-// Bounded wait for one phase of the MMA mbarrier (about 50 ms at most).
+__device__ __forceinline__ uint64_t tc_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for one phase of the MMA mbarrier: gives up after 100 ms of
+// device time (an MMA round trip takes microseconds), with an iteration cap
+// behind it.
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase)
 {
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 20) && !done; ++it)
+    const uint64_t t0 = tc_globaltimer();
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(mbar), "r"(phase)
             : "memory");
+        if (!done && (it & 63) == 63 && tc_globaltimer() - t0 > 100000000ull) break;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     return done != 0;
 }
@@ -286,6 +299,7 @@ __device__ __forceinline__ void tc_zero_pad(int j)
 
 // Per-block state of the tensor-core column pass.
 struct TcState {
+    int no_mma;           // test hook (see P2TcArgs)
     uint32_t bsm;         // shared address of the DFT matrices
     uint32_t tbase;       // TMEM base
     uint32_t mbar;        // shared address of the MMA mbarrier
@@ -314,7 +328,7 @@ struct TcChain<N, Ns, SIdx, LO, Seq<R, Rest...>> {
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         const bool dead = *st.dead != 0;
-        if (!dead && threadIdx.x == 0) {
+        if (!dead && threadIdx.x == 0 && !st.no_mma) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             tc_issue<G>(st.tbase, sm_u32(tc_dsmem), st.bsm + LO::moff(SIdx), st.mbar);
         }
@@ -513,7 +527,7 @@ __global__ void __launch_bounds__(TcPlan<P, N>::THREADS, TcPlan<P, N>::MINB) p2_
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    TcState st{sm_u32(Bs), *tslot, sm_u32(mbar), 0u, dead};
+    TcState st{A.no_mma, sm_u32(Bs), *tslot, sm_u32(mbar), 0u, dead};
 
     for (int c = blockIdx.x; c < a.ncols; c += gridDim.x) tc_column<P, N, KREAL>(A, c, st);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

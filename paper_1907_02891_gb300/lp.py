@@ -34,6 +34,7 @@ EXPORTS = (
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
     "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
+    "lp_set_test_hook",
     "lp_serve_start", "lp_serve_submit", "lp_serve_poll", "lp_serve_stats", "lp_serve_stop",
 )
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_map_workspace_bytes": ([_i, _i, _i, _i, _i, _i, _i, _i], _sz),
         "lp_sync_status": ([_vp, _vp, _i], _i),
         "lp_set_pass_timing": ([_vp, _i], _i),
+        "lp_set_test_hook": ([_vp, _i], _i),
         "lp_map_noalloc": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp], _i),
         "lp_map_noalloc_scratch_bytes": ([], _sz),
         "lp_serve_start": ([_vp, _i], _i),
@@ -258,6 +260,14 @@ def call_status(name: str, *args) -> int:
 
 
 PASS_NAMES = ("p1_rows", "p2_cols", "p3_rows")
+
+
+LP_TEST_TC_NO_MMA = 1
+
+
+def lp_set_test_hook(ctx: int, hook: int) -> None:
+    """Test hooks (failure-detection tests only); 0 clears them."""
+    _check(load_library().lp_set_test_hook(ctx, hook), "lp_set_test_hook")
 
 
 def lp_set_pass_timing(ctx: int, enable: bool) -> None:

@@ -182,3 +182,29 @@ def test_split_precision_rules(ctx):
     lp.lp_sync_status(ctx)
     lp.lp_spectrum_release(ctx, s32)
     lp.lp_spectrum_release(ctx, ssp)
+
+
+def test_split_mma_wait_runs_out_and_context_recovers(ctx):
+    """Failure detection without a fault: with the test hook the tensor-core
+    pass issues no MMA, its bounded wait (100 ms of device time) runs out,
+    the device status word reports it, and the context then maps correctly."""
+    g = np.random.default_rng(24)
+    L = g.lognormal(0.0, 1.0, (60, 70)).astype(np.float32)
+    K = g.uniform(0.1, 1.0, (9, 9))
+    s = lp.lp_kernel_spectrum(ctx, dev(K), max_h=60, max_w=70, prec=SPLIT)
+    out = torch.empty((60, 70), dtype=torch.float32, device=DEV)
+    lp.lp_set_test_hook(ctx, lp.LP_TEST_TC_NO_MMA)
+    try:
+        lp.lp_map(ctx, dev(L), [s], [out], prec=SPLIT)
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_sync_status(ctx, timeout_ms=20000)
+        assert e.value.status == lp.LP_ERR_DEVICE
+    finally:
+        lp.lp_set_test_hook(ctx, 0)
+    lp.lp_map(ctx, dev(L), [s], [out], prec=SPLIT)
+    lp.lp_sync_status(ctx)
+    assert err_maxnorm(out.cpu().numpy(), oracle.conv_same(L, K)) <= TOL_SPLIT
+    with pytest.raises(lp.LpError) as e:
+        lp.lp_set_test_hook(ctx, 0x100)
+    assert e.value.status == lp.LP_ERR_INVALID
+    lp.lp_spectrum_release(ctx, s)
