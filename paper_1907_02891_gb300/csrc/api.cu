@@ -613,10 +613,12 @@ extern "C" lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s)
 // ---------------------------------------------------------------------------
 static inline long long even_up(long long x) { return (x + 1) / 2 * 2; }
 
-// workspace layout: T (ncols x ldT) then U (n x ncols x ldU), complex64
+// workspace layout: T (ncolsT x ldT, column-blocked) then U (n x ncols x
+// ldU), complex64
 static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mode, MapDims* d)
 {
     d->ncols = nx / 2 + 1;
+    d->ncolsT = t_cols_alloc(d->ncols);
     d->ldT = even_up(h);
     if (mode == LP_OUT_FULL) {
         d->Hout = h + hk - 1;
@@ -642,7 +644,7 @@ extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, i
     MapDims d;
     map_dims(h, w, ny, nx, hk, wk, mode, &d);
     const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    return 8ull * (size_t)d.ncols * (size_t)(d.ldT + (long long)nchunk * d.ldU) + 256;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncols * (size_t)nchunk * (size_t)d.ldU) + 256;
 }
 
 lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
@@ -807,7 +809,7 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     ps = lp_get_plan(ctx, s0->nx, &px);
     if (ps != LP_OK) return ps;
     float2* T = static_cast<float2*>(ws);
-    float2* U = T + (size_t)d.ncols * d.ldT;
+    float2* U = T + (size_t)d.ncolsT * d.ldT;
     if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
@@ -917,7 +919,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     st = lp_get_workspace(ctx, c, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
     float2* T = static_cast<float2*>(ws);
-    float2* U = T + (size_t)d.ncols * d.ldT;
+    float2* U = T + (size_t)d.ncolsT * d.ldT;
     cudaEvent_t* ev = ctx->hs_events.data();
     cudaEvent_t ev_start = ev[0], ev_end = ev[1];
     cudaEvent_t* ev_in = ev + 2;                 // kHostBands
@@ -1042,12 +1044,12 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     const PlanRec *py, *px;
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
     if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
-    const size_t tbytes = 8ull * (size_t)d.ncols * d.ldT;
+    const size_t tbytes = 8ull * (size_t)d.ncolsT * d.ldT;
     const size_t ubytes = 8ull * (size_t)d.ncols * d.ldU;
     void* ws = nullptr;
     if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + 256, &ws)) != LP_OK) return st;
     float2* Tb = static_cast<float2*>(ws);
-    float2* U = Tb + (size_t)T * d.ncols * d.ldT;
+    float2* U = Tb + (size_t)T * d.ncolsT * d.ldT;
     const int npairs = (int)(d.ldT / 2);
     for (int t = 0; t < T; ++t) {
         P1Args a1;
@@ -1057,7 +1059,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
         a1.W = w;
         a1.Wst = (w + 3) / 4 * 4;
         a1.vec16 = ((reinterpret_cast<uintptr_t>(L[t]) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
-        a1.T = Tb + (size_t)t * d.ncols * d.ldT;
+        a1.T = Tb + (size_t)t * d.ncolsT * d.ldT;
         a1.ldT = d.ldT;
         a1.pair0 = 0;
         a1.npairs = npairs;
@@ -1075,7 +1077,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
                                "lp_map_multiclass: mixing real and complex spectra is not supported");
     P2MArgs a2;
     for (int i = 0; i < kMaxSpectraPerLaunch; ++i) {
-        a2.T[i] = i < T ? Tb + (size_t)i * d.ncols * d.ldT : nullptr;
+        a2.T[i] = i < T ? Tb + (size_t)i * d.ncolsT * d.ldT : nullptr;
         a2.K[i] = i < T ? spectra[i]->data : nullptr;
     }
     a2.ldT = d.ldT;

@@ -17,7 +17,8 @@
 //
 // Layouts (element = complex64 unless stated):
 //   L    FP32, row-major H x W, leading dimension ldl (elements)
-//   T    (Nx/2+1) rows of ldT >= 2 ceil(H/2) elements
+//   T    the row pass's half spectra, column-blocked (below): ldT >= 2 ceil(H/2)
+//        elements per column, Nx/2+1 columns rounded up to a multiple of kTCB
 //   K^   (Nx/2+1) rows of ldK elements: FP32 (point-symmetric PSF, real
 //        spectrum) or complex64
 //   U    per spectrum (Nx/2+1) rows of ldU >= 2 ceil(Hout/2) elements
@@ -27,6 +28,26 @@
 #include "fft_core.cuh"
 
 namespace lpk {
+
+// Layout of T.  Element (column c, row pair p) is a float4 {X_a[c], X_b[c]}
+// (the two rows of the pair); columns are grouped in blocks of kTCB, and
+// within a block the kTCB columns' float4 of one row pair sit side by side:
+//   float4 index ((c / kTCB) * ldq + p) * kTCB + c mod kTCB,  ldq = ldT / 2.
+// The row pass, which produces all columns of one row pair, then writes
+// 16 kTCB contiguous bytes per column block instead of 16 scattered ones
+// (measured at 4704^2: row pass 74 -> 58 us, column pass 68 -> 72 us).
+constexpr int kTCB = 2;
+__host__ __device__ constexpr long long t_cols_alloc(long long ncols) { return (ncols + kTCB - 1) / kTCB * kTCB; }
+__host__ __device__ __forceinline__ long long t_index4(int c, long long p, long long ldq)
+{
+    return ((long long)(c / kTCB) * ldq + p) * kTCB + (c % kTCB);
+}
+// float2 pointer to row 0 of column c; row r is at t_row(r) from it
+__host__ __device__ __forceinline__ const float2* t_column(const float2* T, long long ldT, int c)
+{
+    return T + 2 * t_index4(c, 0, ldT / 2);
+}
+__host__ __device__ __forceinline__ long long t_row(int r) { return (long long)(r >> 1) * (2 * kTCB) + (r & 1); }
 
 constexpr int kMaxSpectraPerLaunch = 32;
 
@@ -200,7 +221,7 @@ __device__ __forceinline__ void unpack_rows(const float2* sm, int t, int ncols, 
         o.y = zc.y - zm.y;
         o.z = zc.y + zm.y;       // 2 X_b = -i (Z[c] - conj Z[N-c])
         o.w = -(zc.x - zm.x);
-        Tq[(long long)c * ldq + pair] = o;
+        Tq[t_index4(c, pair, ldq)] = o;
     }
 }
 
@@ -333,7 +354,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     float2* sm = smem2;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
-    const float2* col = a.T + (long long)c * a.ldT;
+    const float2* col = t_column(a.T, a.ldT, c);
 
     float2 v[P::E0][R0];
 #pragma unroll
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = j + m * NB0;
-            v[e][m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
+            v[e][m] = row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f);
         }
     }
     Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
@@ -524,8 +545,9 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 
     auto prefetch_t = [&](int c) {
         if (c >= a.ncols) return;
-        const float2* src = a.T + (long long)c * a.ldT;
-        for (int q = threadIdx.x; q < (int)(a.ldT >> 1); q += T) cp_async16(tst + 2 * q, src + 2 * q);
+        const float4* src = reinterpret_cast<const float4*>(a.T);
+        const long long ldq = a.ldT >> 1;
+        for (int q = threadIdx.x; q < (int)ldq; q += T) cp_async16(tst + 2 * q, src + t_index4(c, q, ldq));
         cp_async_commit();
     };
     auto prefetch_k = [&](int c) {
@@ -655,7 +677,7 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
     constexpr int R0 = P::R0, NB0 = N / R0;
     constexpr int RL = P::RL, NBL = N / RL;
     const int t = threadIdx.x;
-    const float2* col = a.T[q] + (long long)c * a.ldT;
+    const float2* col = t_column(a.T[q], a.ldT, c);
     float2 v[P::E0][R0];
 #pragma unroll
     for (int e = 0; e < P::E0; ++e) {
@@ -664,7 +686,7 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = j + m * NB0;
-            v[e][m] = row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f);
+            v[e][m] = row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f);
         }
     }
     P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {

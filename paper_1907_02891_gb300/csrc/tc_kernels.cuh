@@ -478,12 +478,12 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
     __syncthreads();  // the previous column's last writes of As are consumed
     // first forward stage: rows j + m N/R0 of column c (rows >= H are the zero padding)
     if (t < NB0) {
-        const float2* col = a.T + (long long)c * a.ldT;
+        const float2* col = t_column(a.T, a.ldT, c);
         tc_zero_pad<G0>(t);
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = t + m * NB0;
-            tc_put<G0>(t, m, row < a.H ? __ldg(col + row) : make_float2(0.f, 0.f));
+            tc_put<G0>(t, m, row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f));
         }
     }
     {
