@@ -613,12 +613,13 @@ extern "C" lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s)
 // ---------------------------------------------------------------------------
 static inline long long even_up(long long x) { return (x + 1) / 2 * 2; }
 
-// workspace layout: T (ncolsT x ldT, column-blocked) then U (n x ncols x
-// ldU), complex64
+// workspace layout: T (ncolsT x ldT) then U (n x ncolsU x ldU), complex64,
+// both column-blocked
 static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mode, MapDims* d)
 {
     d->ncols = nx / 2 + 1;
     d->ncolsT = t_cols_alloc(d->ncols);
+    d->ncolsU = u_cols_alloc(d->ncols);
     d->ldT = even_up(h);
     if (mode == LP_OUT_FULL) {
         d->Hout = h + hk - 1;
@@ -644,7 +645,7 @@ extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, i
     MapDims d;
     map_dims(h, w, ny, nx, hk, wk, mode, &d);
     const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncols * (size_t)nchunk * (size_t)d.ldU) + 256;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
 }
 
 lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
@@ -725,9 +726,9 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.K[0] = spectra[base + i]->data;
             b.ldK = s0->ldK;
             b.nspec = 1;
-            b.U = U + (size_t)i * d.ncols * d.ldU;
+            b.U = U + (size_t)i * d.ncolsU * d.ldU;
             b.ldU = d.ldU;
-            b.specU = (long long)d.ncols * d.ldU;
+            b.specU = (long long)d.ncolsU * d.ldU;
             b.r0 = d.r0;
             b.Hout = d.Hout;
             b.HoutPad = (int)d.ldU;
@@ -758,9 +759,9 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             a2.K[i] = (i < k1 - k0) ? spectra[base + k0 + i]->data : nullptr;
         a2.ldK = s0->ldK;
         a2.nspec = k1 - k0;
-        a2.U = U + (size_t)k0 * d.ncols * d.ldU;
+        a2.U = U + (size_t)k0 * d.ncolsU * d.ldU;
         a2.ldU = d.ldU;
-        a2.specU = (long long)d.ncols * d.ldU;
+        a2.specU = (long long)d.ncolsU * d.ldU;
         a2.r0 = d.r0;
         a2.Hout = d.Hout;
         a2.HoutPad = (int)d.ldU;
@@ -781,7 +782,7 @@ static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDi
     P3Args a3;
     a3.U = U;
     a3.ldU = d.ldU;
-    a3.specU = (long long)d.ncols * d.ldU;
+    a3.specU = (long long)d.ncolsU * d.ldU;
     a3.Hout = d.Hout;
     a3.pair0 = pair0;
     a3.npairs = pair1;
@@ -1045,7 +1046,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
     if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
     const size_t tbytes = 8ull * (size_t)d.ncolsT * d.ldT;
-    const size_t ubytes = 8ull * (size_t)d.ncols * d.ldU;
+    const size_t ubytes = 8ull * (size_t)d.ncolsU * d.ldU;
     void* ws = nullptr;
     if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + 256, &ws)) != LP_OK) return st;
     float2* Tb = static_cast<float2*>(ws);

@@ -21,7 +21,8 @@
 //        elements per column, Nx/2+1 columns rounded up to a multiple of kTCB
 //   K^   (Nx/2+1) rows of ldK elements: FP32 (point-symmetric PSF, real
 //        spectrum) or complex64
-//   U    per spectrum (Nx/2+1) rows of ldU >= 2 ceil(Hout/2) elements
+//   U    per spectrum, column-blocked (below): ldU >= 2 ceil(Hout/2) elements per
+//        column, Nx/2+1 columns rounded up to a multiple of kUCB
 //   out  FP32 row-major Hout x Wout, leading dimension ldo
 #pragma once
 
@@ -29,25 +30,48 @@
 
 namespace lpk {
 
-// Layout of T.  Element (column c, row pair p) is a float4 {X_a[c], X_b[c]}
-// (the two rows of the pair); columns are grouped in blocks of kTCB, and
-// within a block the kTCB columns' float4 of one row pair sit side by side:
-//   float4 index ((c / kTCB) * ldq + p) * kTCB + c mod kTCB,  ldq = ldT / 2.
-// The row pass, which produces all columns of one row pair, then writes
-// 16 kTCB contiguous bytes per column block instead of 16 scattered ones
-// (measured at 4704^2: row pass 74 -> 58 us, column pass 68 -> 72 us).
-constexpr int kTCB = 2;
-__host__ __device__ constexpr long long t_cols_alloc(long long ncols) { return (ncols + kTCB - 1) / kTCB * kTCB; }
-__host__ __device__ __forceinline__ long long t_index4(int c, long long p, long long ldq)
+// Column-blocked layout of the intermediate half spectra T and U.  Element
+// (column c, row pair p) is a float4 {row 2p, row 2p+1} of column c; the
+// columns are grouped in blocks of CB, and within a block the CB columns'
+// float4 of one row pair sit side by side:
+//   float4 index ((c / CB) * ldq + p) * CB + c mod CB,  ldq = ld / 2,
+// with ld the (even) number of rows stored per column.  The row passes,
+// which handle all columns of one row pair, then move 16 CB contiguous
+// bytes per column block instead of 16 scattered ones; the column pass
+// reads / writes a column at a 16 CB-byte stride.  Measured at 4704^2 for
+// T: row pass 74 -> 58 us, column pass 68 -> 70 us with CB = 2 (with 4 / 8:
+// 55.5 / 53.7 and 74 / 80 us).
+template <int CB>
+__host__ __device__ constexpr long long blk_cols_alloc(long long ncols) { return (ncols + CB - 1) / CB * CB; }
+template <int CB>
+__host__ __device__ __forceinline__ long long blk_index4(int c, long long p, long long ldq)
 {
-    return ((long long)(c / kTCB) * ldq + p) * kTCB + (c % kTCB);
+    return ((long long)(c / CB) * ldq + p) * CB + (c % CB);
 }
-// float2 pointer to row 0 of column c; row r is at t_row(r) from it
+// row r of a column, in float2 from the column's row 0
+template <int CB>
+__host__ __device__ __forceinline__ long long blk_row(int r) { return (long long)(r >> 1) * (2 * CB) + (r & 1); }
+
+constexpr int kTCB = 2;  // T: written by the forward row pass, read by the column pass
+// U (written by the column pass, read by the inverse row pass) stays plain
+// column-major: blocks of 2 took 2.7 us off the inverse row pass and put
+// 3.5 us on the column pass at 4704^2
+constexpr int kUCB = 1;
+__host__ __device__ constexpr long long t_cols_alloc(long long ncols) { return blk_cols_alloc<kTCB>(ncols); }
+__host__ __device__ constexpr long long u_cols_alloc(long long ncols) { return blk_cols_alloc<kUCB>(ncols); }
+__host__ __device__ __forceinline__ long long t_index4(int c, long long p, long long ldq) { return blk_index4<kTCB>(c, p, ldq); }
+__host__ __device__ __forceinline__ long long u_index4(int c, long long p, long long ldq) { return blk_index4<kUCB>(c, p, ldq); }
+__host__ __device__ __forceinline__ long long t_row(int r) { return blk_row<kTCB>(r); }
+__host__ __device__ __forceinline__ long long u_row(int r) { return blk_row<kUCB>(r); }
+// float2 pointer to row 0 of column c
 __host__ __device__ __forceinline__ const float2* t_column(const float2* T, long long ldT, int c)
 {
     return T + 2 * t_index4(c, 0, ldT / 2);
 }
-__host__ __device__ __forceinline__ long long t_row(int r) { return (long long)(r >> 1) * (2 * kTCB) + (r & 1); }
+__host__ __device__ __forceinline__ float2* u_column(float2* U, long long ldU, int c)
+{
+    return U + 2 * u_index4(c, 0, ldU / 2);
+}
 
 constexpr int kMaxSpectraPerLaunch = 32;
 
@@ -201,10 +225,10 @@ __device__ __forceinline__ void store_column(const float2 (&o)[P::EJ][P::R0], in
         for (int m = 0; m < R0; ++m) {
             int rr = j + m * NB0 - r0;
             if (rr < 0) rr += N;
-            if (rr < Hout) Uc[rr] = o[e][m];
+            if (rr < Hout) Uc[u_row(rr)] = o[e][m];
         }
     }
-    if (HoutPad != Hout && t == 0) Uc[Hout] = make_float2(0.f, 0.f);
+    if (HoutPad != Hout && t == 0) Uc[u_row(Hout)] = make_float2(0.f, 0.f);
 }
 
 // P1's split of the packed transform Z (in shared memory, natural order)
@@ -335,7 +359,7 @@ __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, con
     const long long kw = KREAL ? 1 : 2;
     spectrum_product<P, N, KREAL, false>(g, t, static_cast<const float*>(a.K[s]) + (long long)c * a.ldK * kw,
                                          nullptr);
-    float2* Uc = a.U + (long long)s * a.specU + (long long)c * a.ldU;
+    float2* Uc = u_column(a.U + (long long)s * a.specU, a.ldU, c);
     P::InvChain::run(g, t, sm, a.twi, [&](float2(&o)[P::EJ][P::R0], int tt) {
         store_column<P, N>(o, tt, Uc, a.r0, a.Hout, a.HoutPad);
     });
@@ -382,7 +406,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
             const long long kw = KREAL ? 1 : 2;
             spectrum_product<P, N, KREAL, false>(fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * kw,
                                                  nullptr);
-            float2* Uc = a.U + (long long)c * a.ldU;
+            float2* Uc = u_column(a.U, a.ldU, c);
             Inv::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
                 store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
             }, P::SMEM_ELEMS);
@@ -422,7 +446,7 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
             const int k = j + m * NBI;
             const bool lo = k < a.ncols;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (live) q = __ldg(Uq + (long long)(lo ? k : N - k) * ldq + pair);
+            if (live) q = __ldg(Uq + u_index4(lo ? k : N - k, pair, ldq));
             v[e][m] = packed_inverse_input(q, lo, vb);
         }
     }
@@ -582,7 +606,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
                 __syncthreads();  // K^ staging consumed
                 prefetch_k(c + gridDim.x);
             }
-            float2* Uc = a.U + (long long)c * a.ldU;
+            float2* Uc = u_column(a.U, a.ldU, c);
             Inv::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
                 store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);
             }, P::SMEM_ELEMS);
@@ -613,7 +637,7 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
 
     auto prefetch = [&](int pair) {
         if (pair >= a.npairs) return;
-        for (int k = threadIdx.x; k < a.ncols; k += T) cp_async16(ust + k, Uq + (long long)k * ldq + pair);
+        for (int k = threadIdx.x; k < a.ncols; k += T) cp_async16(ust + k, Uq + u_index4(k, pair, ldq));
         cp_async_commit();
     };
 
@@ -731,7 +755,7 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2
 #pragma unroll
         for (int m = 0; m < RL; ++m) acc[e][m] = ACC[j + m * NBL];
     }
-    float2* Uc = a.U + (long long)c * a.ldU;
+    float2* Uc = u_column(a.U, a.ldU, c);
     P::InvChain::run(acc, t, sm, a.twi, [&](float2(&o)[P::EJ][P::R0], int tt) {
         store_column<P, N>(o, tt, Uc, a.r0, a.Hout, a.HoutPad);
     });

@@ -41,6 +41,7 @@ struct Workspace {
 struct MapDims {
     int ncols;          // Nx/2 + 1
     long long ncolsT;   // columns allocated for T (ncols rounded up to its column blocks)
+    long long ncolsU;   // columns allocated per spectrum for U (likewise)
     long long ldT, ldU; // leading dimensions of T and U (complex elements, even)
     int Hout, Wout;     // output size
     int r0, c0;         // first kept row / column of the circular result

@@ -76,7 +76,7 @@ struct ServeState {
 static size_t request_footprint(const MapDims& d, int n)
 {
     const int nchunk = n < 32 ? n : 32;
-    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncols * (size_t)nchunk * (size_t)d.ldU) + 256;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
 }
 
 static void finish_slot(ServeState* S, Slot& sl, lp_status st)

@@ -452,7 +452,7 @@ struct TcStoreSink {
     {
         int rr = t + k * (N / R0) - r0;
         if (rr < 0) rr += N;
-        if (rr < Hout) Uc[rr] = make_float2(z.x, -z.y);  // back from the conjugate domain
+        if (rr < Hout) Uc[u_row(rr)] = make_float2(z.x, -z.y);  // back from the conjugate domain
     }
 };
 
@@ -491,10 +491,10 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
         TcProductSink<N, RL, KREAL, GI0> ps{kcol, t};
         Fwd::run(st, a.twf, A.err, t, ps);
     }
-    float2* Uc = a.U + (long long)c * a.ldU;
+    float2* Uc = u_column(a.U, a.ldU, c);
     TcStoreSink<N, R0> ss{Uc, a.r0, a.Hout, t};
     Inv::run(st, a.twi, A.err, t, ss);
-    if (a.HoutPad != a.Hout && t == 0) Uc[a.Hout] = make_float2(0.f, 0.f);
+    if (a.HoutPad != a.Hout && t == 0) Uc[u_row(a.Hout)] = make_float2(0.f, 0.f);
 }
 
 // The column pass: persistent blocks, one column of one spectrum at a time.
