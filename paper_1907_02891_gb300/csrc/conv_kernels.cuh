@@ -62,6 +62,10 @@ __host__ __device__ constexpr long long u_cols_alloc(long long ncols) { return b
 __host__ __device__ __forceinline__ long long t_index4(int c, long long p, long long ldq) { return blk_index4<kTCB>(c, p, ldq); }
 __host__ __device__ __forceinline__ long long u_index4(int c, long long p, long long ldq) { return blk_index4<kUCB>(c, p, ldq); }
 __host__ __device__ __forceinline__ long long t_row(int r) { return blk_row<kTCB>(r); }
+// offset of row j + m S from row j's when S is even (the pair index moves by
+// m S / 2, the row parity stays): a compile-time multiple of m
+template <int S>
+__host__ __device__ constexpr long long t_row_step() { return (long long)(S / 2) * 2 * kTCB; }
 __host__ __device__ __forceinline__ long long u_row(int r) { return blk_row<kUCB>(r); }
 // float2 pointer to row 0 of column c
 __host__ __device__ __forceinline__ const float2* t_column(const float2* T, long long ldT, int c)
@@ -388,7 +392,8 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = j + m * NB0;
-            v[e][m] = row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f);
+            const long long off = (NB0 % 2 == 0) ? t_row(j) + m * t_row_step<NB0>() : t_row(row);
+            v[e][m] = row < a.H ? __ldg(col + off) : make_float2(0.f, 0.f);
         }
     }
     Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
@@ -710,7 +715,8 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = j + m * NB0;
-            v[e][m] = row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f);
+            const long long off = (NB0 % 2 == 0) ? t_row(j) + m * t_row_step<NB0>() : t_row(row);
+            v[e][m] = row < a.H ? __ldg(col + off) : make_float2(0.f, 0.f);
         }
     }
     P::FwdChain::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {

@@ -483,7 +483,8 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = t + m * NB0;
-            tc_put<G0>(t, m, row < a.H ? __ldg(col + t_row(row)) : make_float2(0.f, 0.f));
+            const long long off = (NB0 % 2 == 0) ? t_row(t) + m * t_row_step<NB0>() : t_row(row);
+            tc_put<G0>(t, m, row < a.H ? __ldg(col + off) : make_float2(0.f, 0.f));
         }
     }
     {
