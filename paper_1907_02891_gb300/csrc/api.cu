@@ -853,6 +853,18 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
 // entry, and the caller's stream waits for the last copy at exit.
 static constexpr int kHostBands = 8;
 
+// Bands of a host map's upload or download: each copy costs a fixed
+// overhead, so bands are at least ~32 MB (2 to kHostBands of them).
+// Measured end to end on the 4096^2 map (67 MB each way): 8 bands 34.7K,
+// 4 bands 37.5K, 2 bands 37.9K Mpix/s.
+static int host_bands(size_t bytes, int npairs)
+{
+    long long nb = (long long)(bytes / (32ull << 20));
+    if (nb < 2) nb = 2;
+    if (nb > kHostBands) nb = kHostBands;
+    return npairs < nb ? npairs : (int)nb;
+}
+
 static lp_status host_streams(lp_ctx* ctx)
 {
     if (ctx->hs_in) return LP_OK;
@@ -943,7 +955,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     for (int k = 0; k < n; ++k) CUDA_TRY(cudaStreamWaitEvent(c, spectra[k]->ready, 0));
 
     const int npairs = (int)(d.ldT / 2);
-    const int nb_in = npairs < kHostBands ? npairs : kHostBands;
+    const int nb_in = host_bands(lbytes, npairs);
     for (int b = 0; b < nb_in; ++b) {
         const int q0 = (int)((long long)npairs * b / nb_in), q1 = (int)((long long)npairs * (b + 1) / nb_in);
         const int r0 = 2 * q0, r1 = (2 * q1 < h) ? 2 * q1 : h;
@@ -957,7 +969,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     CUDA_TRY(cudaEventRecord(ev_lfree, c));  // the staging map may be overwritten after this
     ctx->hs_lfree_valid = true;
     const int opairs = (int)(d.ldU / 2);
-    const int nb_out = opairs < kHostBands ? opairs : kHostBands;
+    const int nb_out = host_bands(obytes * (size_t)n, opairs);
     for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {
         const int cnt = (n - cb) < kMaxSpectraPerLaunch ? (n - cb) : kMaxSpectraPerLaunch;
         if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, c)) != LP_OK) return st;
