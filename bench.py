@@ -527,7 +527,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic,
-                     "algorithmic_bytes_per_launch": per_launch_bytes},
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "frac_of_nominal_8tbs": achieved / 8000.0},
         "passes": {p: {"ms_per_launch": passes[p][0] / max(1, passes[p][1]),
                        "launches": passes[p][1],
                        "algorithmic_gbs": model[p] * pk / max(1, passes[p][1]) /
