@@ -118,7 +118,8 @@ def plan_table_entry(n: int) -> dict:
             f = cand
             break
     return dict(radices=list(r), threads=t, f1=f, f3=f, smem=smem,
-                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True, tt=0, pf=[1, 1, 1], db=[0, 0, 0])
+                upb=[PF_UNITS] * 3, minb=[1, 1, 1], kstage=True, tt=0, pf=[1, 1, 1], db=[0, 0, 0],
+                batch=True)
 
 
 def plan_table() -> Dict[int, dict]:
@@ -136,7 +137,7 @@ def plan_table() -> Dict[int, dict]:
             e.update(radices=list(t["radices"]), threads=threads_for(n, t["radices"]),
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
                      tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
-                     db=list(t.get("db", [0, 0, 0])))
+                     db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -163,6 +164,10 @@ constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
 constexpr bool kKSTAGE = {kstage};
 constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
 constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
+// several spectra: the batched column kernel (forward column parked in shared
+// memory, one product + inverse per spectrum) or one single-spectrum pass per
+// spectrum (forward transform repeated)
+constexpr bool kBatch = {batch};
 constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
 // split-precision tensor-core column pass (0 shared bytes: not available)
 using TP = TcPlan<P, kN>;
@@ -223,11 +228,12 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
         return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a)
                      : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a);
     }}
-    if constexpr (kSmem2 <= kMaxSmem) {{
+    if constexpr (kBatch && kSmem2 <= kMaxSmem) {{
         return kreal ? launch_pdl(p2_cols<P, kN, true, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
                      : launch_pdl(p2_cols<P, kN, false, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
     }} else {{
-        // no room to park the forward column: one pass per spectrum
+        // one single-spectrum pass per spectrum (no room to park the forward
+        // column, or the plan measured this faster)
         for (int i = 0; i < a.nspec; ++i) {{
             P2Args b = a;
             b.K[0] = a.K[i];
@@ -341,6 +347,7 @@ def generate() -> List[str]:
                                kstage="true" if p["kstage"] else "false",
                                pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
                                db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
+                               batch=_b(p.get("batch", True)),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

@@ -86,6 +86,7 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
                              kstage="true" if plan["kstage"] else "false",
                              pf1=B._b(plan["pf"][0]), pf2=B._b(plan["pf"][1]), pf3=B._b(plan["pf"][2]),
                              db1=B._b(plan["db"][0]), db2=B._b(plan["db"][1]), db3=B._b(plan["db"][2]),
+                             batch=B._b(plan.get("batch", True)),
                              rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
     src = os.path.join(d, f"size_{n}.cu")
     with open(src, "w") as fh:
@@ -266,6 +267,21 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
                 db[i], minb[i] = 1, p["minb"][0]
     out.update(db=db, minb=minb, tuned_total_us=sum(best_pass.values()) * 1e3)
     log(f"N={n}: refined db={db} minb={minb} (sum {out['tuned_total_us']:.1f} us)")
+    if nspec > 1:
+        # several spectra: the batched column kernel against one single-
+        # spectrum pass per spectrum
+        p = dict(out, batch=False)
+        lib = build_or_error(p)
+        if isinstance(lib, str):
+            try:
+                t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
+                log(f"  batch=0: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+                if t["p2_cols"] < best_pass["p2_cols"] * 0.99:
+                    best_pass["p2_cols"] = t["p2_cols"]
+                    out.update(batch=False, tuned_total_us=sum(best_pass.values()) * 1e3)
+            except Exception as e:
+                log(f"  skip batch=0: {str(e).splitlines()[-1][:120]}")
+        log(f"N={n}: batch={out.get('batch', True)} (sum {out['tuned_total_us']:.1f} us)")
     return out
 
 
