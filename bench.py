@@ -115,7 +115,10 @@ def kernel_source_sha(extra=(), lengths=()):
     except (OSError, ValueError):
         tuned = {}
     for n in sorted(set(lengths)):
-        h.update(json.dumps(tuned.get(str(n)), sort_keys=True).encode())
+        e = tuned.get(str(n))
+        if isinstance(e, dict):  # knobs only: notes and tuning metadata change no kernel
+            e = {k: v for k, v in e.items() if k not in ("note", "tuned_on", "tuned_total_us")}
+        h.update(json.dumps(e, sort_keys=True).encode())
     return h.hexdigest()[:16]
 
 
