@@ -40,7 +40,8 @@ namespace lpk {
 // bytes per column block instead of 16 scattered ones; the column pass
 // reads / writes a column at a 16 CB-byte stride.  Measured at 4704^2 for
 // T: row pass 74 -> 58 us, column pass 68 -> 70 us with CB = 2 (with 4 / 8:
-// 55.5 / 53.7 and 74 / 80 us).
+// 55.5 / 53.7 and 74 / 80 us).  The CB-1 columns past the last one that
+// padding adds to a partial last block are allocated and never touched.
 template <int CB>
 __host__ __device__ constexpr long long blk_cols_alloc(long long ncols) { return (ncols + CB - 1) / CB * CB; }
 template <int CB>
@@ -53,10 +54,11 @@ template <int CB>
 __host__ __device__ __forceinline__ long long blk_row(int r) { return (long long)(r >> 1) * (2 * CB) + (r & 1); }
 
 constexpr int kTCB = 2;  // T: written by the forward row pass, read by the column pass
-// U (written by the column pass, read by the inverse row pass) stays plain
-// column-major: blocks of 2 took 2.7 us off the inverse row pass and put
-// 3.5 us on the column pass at 4704^2
-constexpr int kUCB = 1;
+// U: written by the column pass, read by the inverse row pass.  Measured
+// (column / inverse row pass, us), blocks of 1 / 2 / 4:
+//   4704^2:   70.3 / 72.4 / 75.5  and  59.7 / 57.0 / 54.9
+//   17280^2:  1049 / 1142 / 1145  and  1225 / 994 / 851
+constexpr int kUCB = 4;
 __host__ __device__ constexpr long long t_cols_alloc(long long ncols) { return blk_cols_alloc<kTCB>(ncols); }
 __host__ __device__ constexpr long long u_cols_alloc(long long ncols) { return blk_cols_alloc<kUCB>(ncols); }
 __host__ __device__ __forceinline__ long long t_index4(int c, long long p, long long ldq) { return blk_index4<kTCB>(c, p, ldq); }

@@ -66,9 +66,9 @@ def test_supported_sizes_cover_the_workloads(lib):
 def test_workspace_model(lib):
     from paper_1907_02891_gb300 import lp
     # T: 2354 x 4096 (2353 columns rounded up to whole 2-column blocks)
-    # + U: 2353 x 4096 complex64 (+ alignment slack)
+    # + U: 2356 x 4096 (whole 4-column blocks), complex64, + alignment slack
     b = lp.lp_map_workspace_bytes(4096, 4096, 4704, 4704, 541, 541, 1)
-    assert b == 8 * (2354 * 4096 + 2353 * 4096) + 256
+    assert b == 8 * (2354 * 4096 + 2356 * 4096) + 256
     assert lp.lp_map_workspace_bytes(0, 4096, 4704, 4704, 541, 541, 1) == 0
 
 
