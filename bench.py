@@ -340,38 +340,55 @@ def cufft_comparator(L, Ks, ny, nx, flush, steps, stream):
             "what": "torch.fft rfft2 (zero-padded) x spectrum -> irfft2 -> crop, FP32, same workload"}
 
 
-def cpu_fft_comparator(L, Ks, ny, nx, reps=2):
-    """The paper's own method on the host cores (bench only, not the product
-    path): zero-padded rfft2 of the map, product with the spectrum of the
-    wrap-placed PSF (computed once, outside the timing), irfft2, crop -- with
-    scipy.fft (pocketfft) on all cores, in FP64 and FP32."""
-    import numpy as np
+def _host_fft():
     try:
         import scipy.fft as sf
-        lib, workers = "scipy.fft (pocketfft)", os.cpu_count() or 1
+        return sf, "scipy.fft (pocketfft)", os.cpu_count() or 1
     except ImportError:
         import numpy.fft as sf
-        lib, workers = "numpy.fft (one thread: scipy absent)", 1
+        return sf, "numpy.fft (one thread: scipy absent)", 1
+
+
+def host_fft_spectrum(K, ny, nx, dtype):
+    """rfft2 of the PSF zero-padded to ny x nx with its centre at (0, 0)."""
+    import numpy as np
+    sf, _, workers = _host_fft()
     kw = {"workers": workers} if workers > 1 else {}
+    hk, wk = K.shape
+    Kw = np.zeros((ny, nx), dtype)
+    Kw[:hk, :wk] = K
+    Kw = np.roll(Kw, (-(hk // 2), -(wk // 2)), axis=(0, 1))
+    return sf.rfft2(Kw, **kw)
+
+
+def host_fft_map(L, khat, ny, nx, dtype):
+    """The paper's method on the host: zero-padded rfft2 of the map, product
+    with the spectrum, irfft2, crop to the map region."""
+    import numpy as np
+    sf, _, workers = _host_fft()
+    kw = {"workers": workers} if workers > 1 else {}
+    H, W = L.shape
+    Lp = np.zeros((ny, nx), dtype)
+    Lp[:H, :W] = L
+    return sf.irfft2(sf.rfft2(Lp, **kw) * khat, s=(ny, nx), **kw)[:H, :W].copy()
+
+
+def cpu_fft_comparator(L, Ks, ny, nx, reps=2):
+    """The paper's own method on the host cores (bench only, not the product
+    path): host_fft_map with scipy.fft (pocketfft) on all cores, in FP64 and
+    FP32; the PSF spectra are computed once, outside the timing."""
+    import numpy as np
+    _, lib, workers = _host_fft()
     H, W = L.shape
     res = {"unit": UNIT, "cores": workers, "kind": lib + " rfft2 / irfft2, same workload and padding",
            "reps": reps}
     for name, rdt, cdt in (("fp64", np.float64, np.complex128), ("fp32", np.float32, np.complex64)):
-        khs = []
-        for K in Ks:
-            hk, wk = K.shape
-            Kw = np.zeros((ny, nx), rdt)
-            Kw[:hk, :wk] = K
-            Kw = np.roll(Kw, (-(hk // 2), -(wk // 2)), axis=(0, 1))
-            khs.append(sf.rfft2(Kw, **kw).astype(cdt))
+        khs = [host_fft_spectrum(K, ny, nx, rdt).astype(cdt) for K in Ks]
         best = None
         for _ in range(reps):
             t0 = time.perf_counter()
-            Lp = np.zeros((ny, nx), rdt)
-            Lp[:H, :W] = L
-            Lh = sf.rfft2(Lp, **kw)
             for kh in khs:
-                sf.irfft2(Lh * kh, s=(ny, nx), **kw)[:H, :W].copy()
+                host_fft_map(L, kh, ny, nx, rdt)
             dt = time.perf_counter() - t0
             best = dt if best is None else min(best, dt)
         res[name] = H * W * len(Ks) / best / 1e6
