@@ -152,8 +152,10 @@ lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s);
 
 /*
  * The map (steps S1-S6): B_k = K_k * L for each of the n spectra, from one
- * shared forward transform of L (Sec. 3 computes several maps -- zenithal
- * brightness and all-sky ratio -- from the same radiance map).
+ * shared row transform of L; the column pass also shares its forward
+ * transform across the spectra where the length's plan batches them (Sec. 3
+ * computes several maps -- zenithal brightness and all-sky ratio -- from the
+ * same radiance map).
  *
  *   L        device FP32, h x w, leading dimension ldl >= w.
  *   spectra  n >= 1 handles with identical (ny, nx), ny >= h + hk - 1 and
