@@ -5,12 +5,14 @@
 //
 //   P1  rows:    two real rows a, b packed as z = a + i b, length-Nx forward
 //                FFT, split into the half spectra of a and b (Hermitian
-//                symmetry), stored transposed: T[c][i], c in [0, Nx/2].
+//                symmetry), stored by column c in [0, Nx/2] (column-blocked
+//                layout, below).
 //   P2  columns: per column c, length-Ny forward FFT of T[c][0..H) (rows
 //                >= H are the zero padding), multiply by the PSF spectrum
 //                K^[c][.] (pre-scaled by 1/(2 Ny Nx)), inverse FFT, keep the
-//                output rows of the crop window.  With n spectra the forward
-//                result stays in registers and is reused n times.
+//                output rows of the crop window.  With n spectra the batched
+//                kernel parks the forward result in shared memory and reuses
+//                it n times; plans may instead run one pass per spectrum.
 //   P3  rows:    Hermitian extension of two rows' half spectra packed as
 //                Z = A + i B, length-Nx inverse FFT, real part -> row a,
 //                imaginary part -> row b, keep the crop columns.
