@@ -638,14 +638,19 @@ static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mo
     d->prec = (int)LP_PREC_FP32;
 }
 
+size_t lp_workspace_bytes(const MapDims& d, int n)
+{
+    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
+}
+
 extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
                                          lp_outmode mode)
 {
     if (h < 1 || w < 1 || ny < 1 || nx < 1 || n < 1 || hk < 1 || wk < 1) return 0;
     MapDims d;
     map_dims(h, w, ny, nx, hk, wk, mode, &d);
-    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
+    return lp_workspace_bytes(d, n);
 }
 
 lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,

@@ -103,6 +103,9 @@ lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out
 lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                           const lp_spectrum* const* spectra, int n, const void* out, int ldo,
                           lp_outmode mode, lp_precision prec, MapDims* d);
+// bytes of one map's workspace: T, then U for up to kMaxSpectraPerLaunch
+// spectra (the spectra of one launch), + alignment slack
+size_t lp_workspace_bytes(const MapDims& d, int n);
 lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                         const MapDims& d, void* ws, cudaStream_t st);

@@ -73,11 +73,7 @@ struct ServeState {
     uint64_t n_done = 0, n_failed = 0;
 };
 
-static size_t request_footprint(const MapDims& d, int n)
-{
-    const int nchunk = n < 32 ? n : 32;
-    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
-}
+
 
 static void finish_slot(ServeState* S, Slot& sl, lp_status st)
 {
@@ -217,7 +213,7 @@ extern "C" lp_status lp_serve_submit(lp_ctx* ctx, const float* L, int h, int w, 
     rq.spectra.assign(spectra, spectra + n);
     rq.out.assign(out, out + n);
     rq.dims = d;
-    rq.footprint = request_footprint(d, n);
+    rq.footprint = lp_workspace_bytes(d, n);
     rq.submitted = Clock::now();
     {
         std::lock_guard<std::mutex> g(S->mu);
