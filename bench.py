@@ -107,8 +107,11 @@ def kernel_source_sha(extra=(), lengths=()):
     given FFT lengths (the plans of other lengths do not change them)."""
     h = hashlib.sha1()
     for p in KERNEL_SOURCES + tuple(extra):
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as fh:
+            for line in fh:  # whole-line comments and blank lines change no kernel
+                t = line.strip()
+                if t and not t.startswith(("//", "#", "/*", "*")):
+                    h.update(t.encode())
     try:
         with open(os.path.join(ROOT, TUNED_PLANS)) as fh:
             tuned = json.load(fh)

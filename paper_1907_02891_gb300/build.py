@@ -257,7 +257,9 @@ cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 }}
 
 // persistent grid of the tensor-core column pass: resident blocks per SM
-// (registers, shared memory, threads, TMEM columns) times the SMs
+// (registers, shared memory, threads, TMEM columns) times the SMs, computed
+// once, for the device of the first launch (a different GPU model in the
+// same process would only get a less fitting grid, never a wrong result)
 template <bool KREAL>
 int tc_grid(int ncols)
 {{
