@@ -5,10 +5,17 @@ each with one candidate radix sequence and one setting of the launch knobs
 of the prefetching kernels (work units per block, minimum resident blocks per
 SM, spectrum-column staging), times the three passes of a map whose padded
 size is N x N on the GPU, and keeps, for the fastest radix sequence, the best
-knob setting of each pass.  The result is written to ``tuned_plans.json``
+knob setting of each pass, then refines it (double-buffered exchange; with
+several spectra per map, one single-spectrum column pass per spectrum
+against the batched kernel).  The result is written to ``tuned_plans.json``
 beside this file; ``build.py`` uses it for every length it lists.
 
-    python -m paper_1907_02891_gb300.tune --sizes 4704 8820 [--quick]
+    python -m paper_1907_02891_gb300.tune --sizes 4704 [--quick] \
+        [--map-side 4096 --psf 541 --nspec 1] [--plan 21,16,14 ...]
+
+The passes are timed one by one, with events between them, which stops the
+launch overlap between passes of a real map; check a stored plan on the
+whole map as well (a setting that speeds one pass up can slow the map down).
 
 Needs nvcc and one GPU.  Each variant is timed in a fresh subprocess (the
 variant libraries export the same symbols).
@@ -184,6 +191,7 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
                          minb=[minb] * 3, kstage=kst, tt=tt, pf=[pf] * 3, db=[0, 0, 0])
                 variants.append(p)
     t0 = time.time()
+
     def build_or_error(p):
         try:
             return _variant_lib(n, p, common)
