@@ -67,6 +67,11 @@ def parse_args():
     ap.add_argument("--load", type=float, default=0.7,
                     help="offered load as a fraction of the measured back-to-back capacity")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--forms", default="batched,split_bf16,serve",
+                    help="forms measured beside the headline map (comma list; empty: none): "
+                         "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
+                         "serve (Poisson requests at 130%% load)")
+    ap.add_argument("--forms-serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -398,6 +403,152 @@ def cpu_fft_comparator(L, Ks, ny, nx, reps=2):
     return res
 
 
+def _time_maps(lp, ctx, L, specs, outs, prec, steps, warmup, flush, stream, per_spectrum=False):
+    """Device ms of each of `steps` maps (CUDA events on the launching stream
+    around each call, L2 flushed between calls outside the events).  With
+    per_spectrum, a step is one single-spectrum call per spectrum (the plain
+    path without a shared forward transform)."""
+    import torch
+
+    def one():
+        if per_spectrum:
+            for s, o in zip(specs, outs):
+                lp.lp_map(ctx, L, [s], [o], prec=prec)
+        else:
+            lp.lp_map(ctx, L, specs, outs, prec=prec)
+
+    for _ in range(warmup):
+        flush.zero_()
+        one()
+    lp.lp_sync_status(ctx)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        one()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    lp.lp_sync_status(ctx)
+    return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+def _time_passes(lp, ctx, L, specs, outs, prec, pk, flush):
+    """Per-pass durations from the library's pass events over pk maps (a loop
+    of its own: events between the passes stop their launch overlap)."""
+    lp.lp_set_pass_timing(ctx, True)
+    lp.lp_get_pass_timing(ctx)
+    for _ in range(pk):
+        flush.zero_()
+        lp.lp_map(ctx, L, specs, outs, prec=prec)
+    lp.lp_sync_status(ctx)
+    passes = lp.lp_get_pass_timing(ctx)
+    lp.lp_set_pass_timing(ctx, False)
+    return passes
+
+
+def _roofline(passes, model, pk, peak):
+    """Dominant pass: algorithmic bytes per launch (3-pass model x units per
+    launch) / its average event-timed launch duration."""
+    dom = max(PASSES, key=lambda p: passes[p][0])
+    ms_tot, launches = passes[dom]
+    per_launch_s = ms_tot / 1e3 / max(1, launches)
+    per_launch_bytes = model[dom] * (pk / max(1, launches))
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    return dom, achieved, per_launch_bytes, achieved / peak
+
+
+def _pass_table(passes, model, pk):
+    return {p: {"ms_per_launch": passes[p][0] / max(1, passes[p][1]), "launches": passes[p][1],
+                "algorithmic_gbs": model[p] * pk / max(1, passes[p][1]) /
+                (passes[p][0] / 1e3 / max(1, passes[p][1])) / 1e9}
+            for p in PASSES}
+
+
+def cpu_baseline_leg_error(L, Ks, outs, seed, n=4096, top=64):
+    """The CPU-baseline leg's accuracy check: max |B - B_ref| / max |B_ref| of
+    the GPU maps against the FP64 direct sum (the oracle), on n seeded pixels
+    plus the `top` brightest pixels of each GPU output (so that the
+    denominator is the map maximum).  Runs outside every timed region."""
+    import numpy as np
+    import oracle
+    import synth
+    H, W = L.shape
+    worst = 0.0
+    for k, (K, o) in enumerate(zip(Ks, outs)):
+        B = o.cpu().numpy()
+        ii, jj = synth.sample_pixels(H, W, n, seed + k)
+        flat = np.argpartition(B.ravel(), -top)[-top:]
+        ii = np.concatenate([ii, flat // W])
+        jj = np.concatenate([jj, flat % W])
+        ref = oracle.conv_points_same(L, K, ii, jj)
+        err = float(np.max(np.abs(B[ii, jj].astype(np.float64) - ref)) / np.max(np.abs(ref)))
+        worst = max(worst, err)
+    return worst
+
+
+def _form_map(lp, args, wl, prec_name, flush, stream, dev, compare_fp32=True, per_spectrum_plain=False):
+    """One 'form' of the path on its own workload: Mpix/s, the dominant pass's
+    roofline fraction on its byte model, the error against the oracle, and
+    the plain FP32 path on the same workload beside it."""
+    import torch
+    peak, peak_kind = measured_peak()
+    H, W = wl.H, wl.W
+    L_host = wl.radiance()
+    Ks = wl.psfs()
+    n = len(Ks)
+    hk_max = max(K.shape[0] for K in Ks)
+    ctx = lp.lp_create(dev.index or 0)
+    try:
+        L = torch.from_numpy(L_host).to(dev)
+        split = prec_name == "split_bf16"
+        prec = lp.LP_PREC_SPLIT_BF16 if split else lp.LP_PREC_FP32
+        ny = lp.lp_supported_size(H + hk_max - 1)
+        if split:
+            ny = min(n_ for n_ in lp.supported_sizes() if n_ >= H + hk_max - 1 and lp.lp_split_supported(n_))
+        nx = lp.lp_supported_size(W + hk_max - 1)
+        Kd = [torch.from_numpy(K).to(dev) for K in Ks]
+        specs = [lp.lp_kernel_spectrum(ctx, K, pad_ny=ny, pad_nx=nx, prec=prec) for K in Kd]
+        info = lp.lp_spectrum_info(specs[0])
+        s_k = 4 if info["is_real"] else 8
+        outs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(n)]
+        steps, warm = max(3, min(args.steps, 20)), max(3, min(args.warmup, 5))
+        ms = statistics.mean(_time_maps(lp, ctx, L, specs, outs, prec, steps, warm, flush, stream))
+        pk = min(args.steps, 50)
+        passes = _time_passes(lp, ctx, L, specs, outs, prec, pk, flush)
+        model = pass_bytes(H, W, ny, nx, n, s_k)
+        dom, achieved, per_launch, frac = _roofline(passes, model, pk, peak)
+        err = cpu_baseline_leg_error(L_host, Ks, outs, wl.seed + 300)
+        rec = {"workload": wl.name, "map": f"{H}x{W}", "psf": f"{wl.psf_side}x{wl.psf_side}", "n_psf": n,
+               "padded": f"{ny}x{nx}", "precision": prec_name, "mpix_s": H * W * n / (ms / 1e3) / 1e6,
+               "ms_per_step": ms, "steps": steps,
+               "roofline": {"kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": frac, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": per_launch},
+               "passes": _pass_table(passes, model, pk), "max_norm_err": err,
+               "tolerance": 2e-4 if split else 1e-5}
+        for s in specs:
+            lp.lp_spectrum_release(ctx, s)
+        # the plain FP32 path on the same workload: FP32 spectra, and for the
+        # batched form one single-spectrum call per PSF (no shared transform)
+        if compare_fp32:
+            nyp = lp.lp_supported_size(H + hk_max - 1)
+            sp = [lp.lp_kernel_spectrum(ctx, K, pad_ny=nyp, pad_nx=nx) for K in Kd]
+            pms = statistics.mean(_time_maps(lp, ctx, L, sp, outs, lp.LP_PREC_FP32, steps, warm, flush, stream,
+                                             per_spectrum=per_spectrum_plain))
+            rec["plain_fp32"] = {"mpix_s": H * W * n / (pms / 1e3) / 1e6, "ms_per_step": pms,
+                                 "padded": f"{nyp}x{nx}",
+                                 "what": ("one single-spectrum map call per PSF" if per_spectrum_plain
+                                          else "FP32 column pass")}
+            rec["speedup_vs_plain_fp32"] = rec["mpix_s"] / rec["plain_fp32"]["mpix_s"]
+            for s in sp:
+                lp.lp_spectrum_release(ctx, s)
+        lp.lp_sync_status(ctx)
+        return rec
+    finally:
+        lp.lp_destroy(ctx)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -469,27 +620,13 @@ def run_ours(args, rank, world, local_rank):
     dev_ms = max_over_ranks(dev_ms, dev)
     value = whole_job_mpix_s(float(H) * W * n, args.steps, world, dev_ms)
 
-    # per-pass durations: a second loop of the same steps with the library's
-    # pass events (CUDA events on the launching stream around each pass)
+    # per-pass durations and the roofline of the dominant pass
     pk = min(args.steps, 500)
-    lp.lp_set_pass_timing(ctx, True)
-    lp.lp_get_pass_timing(ctx)
-    for _ in range(pk):
-        flush.zero_()
-        lp.lp_map(ctx, L, specs, outs, prec=prec)
-    lp.lp_sync_status(ctx)
-    passes = lp.lp_get_pass_timing(ctx)
-    lp.lp_set_pass_timing(ctx, False)
+    passes = _time_passes(lp, ctx, L, specs, outs, prec, pk, flush)
     launches_per_step = sum(passes[p][1] for p in PASSES) / pk
-
-    # roofline of the dominant pass
     model = pass_bytes(H, W, ny, nx, n, s_k)
-    dom = max(PASSES, key=lambda p: passes[p][0])
-    ms_tot, launches = passes[dom]
-    per_launch_s = ms_tot / 1e3 / max(1, launches)
-    per_launch_bytes = model[dom] * (pk / max(1, launches))
-    achieved = per_launch_bytes / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
+    dom, achieved, per_launch_bytes, frac = _roofline(passes, model, pk, peak)
     traffic = dram_traffic(dom + ("_tc" if prec != lp.LP_PREC_FP32 and dom == "p2_cols" else ""), wl.name,
                            (ny, nx))
 
@@ -528,8 +665,12 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_fft:
         cpu_fft = cpu_fft_comparator(L_host, Ks, ny, nx)
 
+    # CPU-baseline leg (rank 0, N = 1): the oracle's accuracy check of this
+    # run's maps, then the oracle timed on the host cores
     cpu = None
+    max_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        max_err = cpu_baseline_leg_error(L_host, Ks, outs, wl.seed + 100)
         rate, npx, secs, cores = oracle_rate(L_host, Ks[0], args.cpu_seconds, wl.seed + 7)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{npx} seeded output pixels of the {H}x{W} map with the first "
@@ -538,6 +679,23 @@ def run_ours(args, rank, world, local_rank):
     for s in specs:
         lp.lp_spectrum_release(ctx, s)
     lp.lp_destroy(ctx)
+
+    # the batched, split-precision and served forms, each beside the plain
+    # FP32 path on the same GPU (rank 0, N = 1)
+    forms = None
+    if rank == 0 and world == 1 and args.forms and not args.no_cpu_baseline:
+        forms = {}
+        want = set(args.forms.split(","))
+        if "batched" in want:
+            forms["batched"] = _form_map(lp, args, synth.WORKLOADS["map8192_psf601x16"], "fp32", flush,
+                                         stream, dev, per_spectrum_plain=True)
+            forms["batched"]["what"] = ("one call, 16 spectra: one forward row transform shared by all, "
+                                        "plain = 16 single-spectrum calls")
+        if "split_bf16" in want:
+            forms["split_bf16"] = _form_map(lp, args, synth.WORKLOADS["map16384_psf801"], "split_bf16",
+                                            flush, stream, dev)
+        if "serve" in want:
+            forms["serve"] = serve_measure(args.forms_serve_requests, 1.3, args.slots, local_rank)
     if rank != 0:
         return
     line = {
@@ -547,22 +705,20 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32" if prec == lp.LP_PREC_FP32 else "bf16-split (hi/lo) products, f32 accumulate",
         "data": "synthetic", "config": dict(workload_config(wl, (ny, nx)),
                        **({} if prec == lp.LP_PREC_FP32 else {"precision": args.prec})),
+        "max_norm_err": max_err,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": frac, "peak_kind": peak_kind,
                      "traffic": traffic,
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "frac_of_nominal_8tbs": achieved / 8000.0},
-        "passes": {p: {"ms_per_launch": passes[p][0] / max(1, passes[p][1]),
-                       "launches": passes[p][1],
-                       "algorithmic_gbs": model[p] * pk / max(1, passes[p][1]) /
-                       (passes[p][0] / 1e3 / max(1, passes[p][1])) / 1e9}
-                   for p in PASSES},
+        "passes": _pass_table(passes, model, pk),
         "whole_step_gbs": sum(model.values()) / (dev_ms / args.steps / 1e3) / 1e9 / world,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "pass_timing": f"per-pass CUDA events in a second loop of {pk} steps (the timed loop has none)",
         "cufft_comparator": cufft, "cpu_fft_comparator": cpu_fft,
         "spectrum_build_ms": s0_ms, "wall_s": wall_s,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
 
@@ -571,19 +727,19 @@ def run_ours(args, rank, world, local_rank):
 # serving run
 # ----------------------------------------------------------------------------
 
-def run_serve(args, rank, world, local_rank):
+def serve_measure(n_requests, load, slots, local_rank, check=True):
     """Poisson arrivals of map requests (tile side uniform on 256..8192, 1-8
     PSFs of a bank of 8 cached 201^2 spectra) through the request scheduler;
     p50/p99 latency and Mpix/s.  The same requests run back to back through
-    lp_map on one stream give the queue-alone reference."""
+    lp_map on one stream give the queue-alone reference.  With `check`, the
+    last requests' outputs are compared bitwise with the same requests run
+    alone, and the last one against the oracle (CPU-baseline leg)."""
     import threading
     import numpy as np
     import torch
     import synth
     from paper_1907_02891_gb300 import lp
 
-    if rank != 0:
-        return
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ctx = lp.lp_create(local_rank)
@@ -619,13 +775,13 @@ def run_serve(args, rank, world, local_rank):
     seq_s = e0.elapsed_time(e1) / 1e3
     seq_mpix = px_probe / seq_s / 1e6
     mean_service = seq_s / len(probe)
-    rate = args.load / mean_service
+    rate = load / mean_service
 
-    reqs = synth.request_stream(args.requests, rate)
-    lp.lp_serve_start(ctx, args.slots)
+    reqs = synth.request_stream(n_requests, rate)
+    lp.lp_serve_start(ctx, slots)
     # warm every slot's workspace with the largest request
     big = max(reqs, key=lambda q: (q.side, len(q.kernels)))
-    warm = [lp.lp_serve_submit(ctx, *call_args(big, k)) for k in range(args.slots)]
+    warm = [lp.lp_serve_submit(ctx, *call_args(big, k)) for k in range(slots)]
     for t in warm:
         lp.lp_serve_poll(ctx, t)
     tickets = [None] * len(reqs)
@@ -665,10 +821,27 @@ def run_serve(args, rank, world, local_rank):
             by_side[str(s)] = {"n": int(sel.sum()), "p50_ms": float(np.percentile(lat_ms[sel], 50)),
                                "p99_ms": float(np.percentile(lat_ms[sel], 99)),
                                "max_ms": float(lat_ms[sel].max())}
+    same, err = None, None
+    if check:
+        # the last `ring` requests' buffers are still intact: rerun each alone
+        same = True
+        for r in range(max(0, len(reqs) - ring), len(reqs)):
+            L, sp, o = call_args(reqs[r], r)
+            alone = [torch.empty_like(x) for x in o]
+            lp.lp_map(ctx, L, sp, alone)
+            lp.lp_sync_status(ctx)
+            same = same and all(torch.equal(x, y) for x, y in zip(o, alone))
+        rq = reqs[-1]
+        L, sp, o = call_args(rq, len(reqs) - 1)
+        bank_np = synth.serve_bank()
+        err = cpu_baseline_leg_error(L.cpu().numpy(), [bank_np[i] for i in rq.kernels], o,
+                                     synth.SERVE_SEED + 500)
     line = {
         "metric": "serve p50/p99 ms", "value": float(np.percentile(lat_ms, 50)),
         "p99_ms": float(np.percentile(lat_ms, 99)), "unit": "ms", "higher_is_better": False,
-        "n_gpus": 1, "requests": len(reqs), "slots": args.slots, "offered_load": args.load,
+        "n_gpus": 1, "requests": len(reqs), "slots": slots, "offered_load": load,
+        "same_as_alone_bitwise": same, "max_norm_err": err,
+        "speedup_vs_back_to_back": (px / makespan / 1e6) / seq_mpix,
         "arrival_rate_hz": rate, "served_mpix_s": px / makespan / 1e6,
         "back_to_back_mpix_s": seq_mpix, "mean_service_ms": 1e3 * mean_service,
         "makespan_s": makespan, "max_ms": float(lat_ms.max()), "by_side": by_side,
@@ -677,8 +850,14 @@ def run_serve(args, rank, world, local_rank):
                    "psf": "201x201", "kernels_per_request": "1-8", "arrivals": "Poisson"},
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     lp.lp_destroy(ctx)
+    return line
+
+
+def run_serve(args, rank, world, local_rank):
+    if rank != 0:
+        return
+    print(json.dumps(serve_measure(args.requests, args.load, args.slots, local_rank)), flush=True)
 
 
 def main():

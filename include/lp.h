@@ -127,6 +127,11 @@ int lp_split_supported(int n);
  *              synchronises the stream once (symmetry check).
  *   out        receives a handle (refcounted: an identical request --
  *              same values, sizes and precision -- returns the cached one).
+ *              The cache is keyed by a 64-bit fingerprint of K's values
+ *              and the sizes; a hit is confirmed by comparing K with a
+ *              device copy kept with the spectrum, value by value, so a
+ *              fingerprint collision builds a new spectrum instead of
+ *              returning another PSF's.
  *
  * A point-symmetric K (K[cy+a][cx+b] == K[cy-a][cx-b] exactly) has a real
  * spectrum and is stored as 4 bytes per bin, otherwise 8.
@@ -147,7 +152,14 @@ lp_status lp_spectrum_info(const lp_spectrum* s, int* ny, int* nx, int* hk, int*
  */
 lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t dst_floats, void* stream);
 
-/* Drop one reference; the spectrum is freed when the last one goes. */
+/*
+ * Drop one reference.  When the last one goes the handle becomes invalid at
+ * once, but the device memory is freed in stream order: only after the
+ * spectrum's build and every map call already enqueued with it (on any
+ * stream) have completed.  The call never waits for the device; memory
+ * still held is freed by a later lp_kernel_spectrum, lp_spectrum_release,
+ * lp_map or lp_sync_status call, or by lp_destroy.
+ */
 lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s);
 
 /*
@@ -168,7 +180,10 @@ lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s);
  *            launch per spectrum; the row passes stay FP32).
  * Asynchronous on `stream`; use lp_sync_status to wait and collect device
  * anomalies.  Calls on different streams of one context may overlap; each
- * stream gets its own workspace.
+ * stream gets its own workspace.  The map waits, in stream order, for the
+ * builds of its spectra (lp_kernel_spectrum is asynchronous on the stream it
+ * is given, and a cache hit may return a spectrum still being built on
+ * another stream); no wait is issued once a build has been seen complete.
  */
 lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                  const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
@@ -251,21 +266,26 @@ lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
  * context stays usable.  0 clears the hooks; unknown bits: LP_ERR_INVALID.
  */
 #define LP_TEST_TC_NO_MMA 1
+/* LP_TEST_FP_COLLIDE: every PSF gets the same cache fingerprint, so that
+ * the value comparison that confirms a cache hit is what tells PSFs apart. */
+#define LP_TEST_FP_COLLIDE 2
 lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
 
 /*
  * Serving: continuous batching of map requests.  lp_serve_start creates
  * n_slots CUDA streams (each with its own workspace) and a scheduler thread.
- * lp_serve_submit validates a request exactly like lp_map (LP_OUT_* mode,
- * FP32) and queues it; the scheduler starts queued requests in arrival order
+ * lp_serve_submit validates a request exactly like lp_map (LP_OUT_* mode;
+ * the precision is the spectra's: LP_PREC_FP32, or LP_PREC_SPLIT_BF16 when
+ * all of them were built in it) and queues it, holding a reference on each
+ * spectrum until the request has finished; the scheduler starts queued requests in arrival order
  * as soon as a slot is free and the request's workspace fits, next to the
  * requests already running, into the serving capacity (the context's HBM
  * budget minus what it holds at start, or 90 % of the free device memory
  * when the context has no budget).  Requests admitted while others run
  * overlap with them on the device.  A request larger than the capacity is
  * refused at submission (LP_ERR_OOM); a full queue gives LP_ERR_BUSY.
- * The caller keeps L, the spectra and out[] alive until the request is
- * polled as finished.
+ * The caller keeps L and out[] alive until the request is polled as
+ * finished; the spectra may be released at any time after submission.
  *
  * lp_serve_poll waits up to timeout_ms (< 0: no limit) for a ticket:
  * LP_OK with the latency (submission to completion, milliseconds, host

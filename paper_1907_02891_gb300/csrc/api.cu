@@ -112,6 +112,8 @@ struct DeviceGuard {
 };
 }  // namespace
 
+static void free_spectrum(lp_ctx* ctx, lp_spectrum* s);
+
 // ---------------------------------------------------------------------------
 // context internals
 // ---------------------------------------------------------------------------
@@ -390,12 +392,10 @@ extern "C" void lp_destroy(lp_ctx* ctx)
     DeviceGuard dg(ctx->device);
     lp_serve_shutdown(ctx);
     cudaDeviceSynchronize();
-    for (auto& kv : ctx->spectra) {
-        lp_ctx_free(ctx, kv.second->data, kv.second->bytes);
-        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
-        delete kv.second;
-    }
+    for (auto& kv : ctx->spectra) free_spectrum(ctx, kv.second);
     ctx->spectra.clear();
+    for (lp_spectrum* sp : ctx->released) free_spectrum(ctx, sp);
+    ctx->released.clear();
     for (auto& w : ctx->ws) lp_ctx_free(ctx, w.ptr, w.bytes);
     ctx->ws.clear();
     for (auto& kv : ctx->plans) lp_ctx_free(ctx, kv.second->tw, kv.second->bytes);
@@ -476,24 +476,58 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     s0 = lp_get_plan(ctx, Nx, &pr);
     if (s0 != LP_OK) return s0;
 
-    // fingerprint + symmetry (one small device round trip)
+    // fingerprint + symmetry (one small device round trip); the third word
+    // holds the flag of the value comparisons below
     unsigned long long* d_fp = nullptr;
-    CUDA_TRY(cudaMallocAsync((void**)&d_fp, 16, st));
-    CUDA_TRY(cudaMemsetAsync(d_fp, 0, 16, st));
+    CUDA_TRY(cudaMallocAsync((void**)&d_fp, 24, st));
+    CUDA_TRY(cudaMemsetAsync(d_fp, 0, 24, st));
     CUDA_TRY(psf_fingerprint_launch(K, (long long)hk * wk, d_fp, st));
     CUDA_TRY(psf_symmetry_launch(K, hk, wk, reinterpret_cast<int*>(d_fp + 1), st));
     unsigned long long host_fp[2] = {0, 0};
     CUDA_TRY(cudaMemcpyAsync(host_fp, d_fp, 16, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    CUDA_TRY(cudaFreeAsync(d_fp, st));
     const int is_real = (int)(host_fp[1] & 0xffffffffull) == 0;
-    const SpecKey key{host_fp[0], hk, wk, Ny, Nx, (int)prec};
+    if (ctx->test_hook & LP_TEST_FP_COLLIDE) host_fp[0] = 0;
+    const SpecKey key0{host_fp[0], hk, wk, Ny, Nx, (int)prec, 0};
+    int* d_diff = reinterpret_cast<int*>(d_fp + 2);
+
+    // Cached spectra of the same fingerprint and sizes, confirmed by comparing
+    // K with each one's stored copy value by value (a fingerprint collision
+    // never returns another PSF's spectrum).  Called with spec_mu held.
+    auto find_cached = [&](lp_spectrum** hit, int* next_salt) -> lp_status {
+        *hit = nullptr;
+        *next_salt = 0;
+        SpecKey lo = key0;
+        lo.salt = -1;
+        for (auto it = ctx->spectra.upper_bound(lo); it != ctx->spectra.end() && it->first.same_request(key0); ++it) {
+            if (it->first.salt + 1 > *next_salt) *next_salt = it->first.salt + 1;
+            int diff = 1;
+            CUDA_TRY(cudaStreamWaitEvent(st, it->second->ready, 0));  // its copy of K is in place
+            CUDA_TRY(cudaMemsetAsync(d_diff, 0, sizeof(int), st));
+            CUDA_TRY(psf_compare_launch(K, it->second->kcopy, (long long)hk * wk, d_diff, st));
+            CUDA_TRY(cudaMemcpyAsync(&diff, d_diff, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (diff == 0) {
+                *hit = it->second;
+                return LP_OK;
+            }
+        }
+        return LP_OK;
+    };
+    lp_reap_released(ctx, false);
+    int salt = 0;
     {
         std::lock_guard<std::mutex> g(ctx->spec_mu);
-        auto it = ctx->spectra.find(key);
-        if (it != ctx->spectra.end()) {
-            it->second->refcount++;
-            *out = it->second;
+        lp_spectrum* hit = nullptr;
+        const lp_status fs = find_cached(&hit, &salt);
+        if (fs != LP_OK) {
+            cudaFreeAsync(d_fp, st);
+            return fs;
+        }
+        if (hit) {
+            hit->refcount++;
+            *out = hit;
+            CUDA_TRY(cudaFreeAsync(d_fp, st));
             return LP_OK;
         }
     }
@@ -501,9 +535,12 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     const long long ldK = ((long long)Ny + 31) / 32 * 32;
     const size_t bytes = (size_t)ncols * ldK * (is_real ? 4 : 8);
     auto spec = new (std::nothrow) lp_spectrum();
-    if (!spec) return lp_fail(LP_ERR_OOM, "host allocation failed");
+    if (!spec) {
+        cudaFreeAsync(d_fp, st);
+        return lp_fail(LP_ERR_OOM, "host allocation failed");
+    }
     spec->ctx = ctx;
-    spec->key = key;
+    spec->key = key0;
     spec->ny = Ny;
     spec->nx = Nx;
     spec->hk = hk;
@@ -512,52 +549,71 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     spec->prec = prec;
     spec->ldK = ldK;
     spec->bytes = bytes;
+    spec->kbytes = sizeof(double) * (size_t)hk * wk;
     spec->refcount = 1;
+    auto discard = [&](lp_spectrum* sp) {
+        cudaStreamSynchronize(st);
+        free_spectrum(ctx, sp);
+    };
     void* dptr = nullptr;
     lp_status sa = lp_ctx_alloc(ctx, bytes, &dptr);
-    if (sa != LP_OK) {
-        delete spec;
-        return sa;
+    if (sa == LP_OK) {
+        spec->data = dptr;
+        void* kc = nullptr;
+        sa = lp_ctx_alloc(ctx, spec->kbytes, &kc);
+        spec->kcopy = static_cast<double*>(kc);
     }
-    spec->data = dptr;
+    if (sa != LP_OK) {
+        const std::string msg = lp_last_error();
+        cudaFreeAsync(d_fp, st);
+        discard(spec);
+        return lp_fail(sa, "%s", msg.c_str());
+    }
     // FP64 scratch, stream-ordered, released right after the build
     const size_t w1 = sizeof(double2) * (size_t)hk * Nx;
     const size_t w2 = sizeof(double2) * (size_t)Ny * ncols;
     char* scratch = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&scratch, 2 * w1 + 2 * w2, st);
     if (e != cudaSuccess) {
-        lp_ctx_free(ctx, dptr, bytes);
-        delete spec;
+        cudaGetLastError();
+        cudaFreeAsync(d_fp, st);
+        discard(spec);
         return lp_fail(LP_ERR_OOM, "spectrum scratch (%zu bytes): %s", 2 * w1 + 2 * w2, cudaGetErrorString(e));
     }
-    cudaMemsetAsync(dptr, 0, bytes, st);
-    e = psf_spectrum_build(K, hk, wk, Ny, Nx, is_real, dptr, ldK, (double2*)scratch,
-                           (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
-                           (double2*)(scratch + 2 * w1 + w2), st);
+    e = cudaMemcpyAsync(spec->kcopy, K, spec->kbytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dptr, 0, bytes, st);
+    if (e == cudaSuccess)
+        e = psf_spectrum_build(K, hk, wk, Ny, Nx, is_real, dptr, ldK, (double2*)scratch,
+                               (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
+                               (double2*)(scratch + 2 * w1 + w2), st);
     cudaFreeAsync(scratch, st);
+    for (int i = 0; e == cudaSuccess && i < lp_spectrum::kUseSlots; ++i)
+        e = cudaEventCreateWithFlags(&spec->use_event[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&spec->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(spec->ready, st);
     if (e != cudaSuccess) {
-        cudaStreamSynchronize(st);
-        lp_ctx_free(ctx, dptr, bytes);
-        if (spec->ready) cudaEventDestroy(spec->ready);
-        delete spec;
+        cudaFreeAsync(d_fp, st);
+        discard(spec);
         return lp_fail(LP_ERR_CUDA, "spectrum build: %s", cudaGetErrorString(e));
     }
     {
         std::lock_guard<std::mutex> g(ctx->spec_mu);
-        auto it = ctx->spectra.find(key);
-        if (it != ctx->spectra.end()) {  // another thread built the same one meanwhile
-            it->second->refcount++;
-            *out = it->second;
-            cudaStreamSynchronize(st);
-            lp_ctx_free(ctx, dptr, bytes);
-            cudaEventDestroy(spec->ready);
-            delete spec;
-            return LP_OK;
+        // another thread may have built the same PSF meanwhile
+        lp_spectrum* hit = nullptr;
+        const lp_status fs = find_cached(&hit, &salt);
+        if (fs != LP_OK || hit) {
+            if (hit) {
+                hit->refcount++;
+                *out = hit;
+            }
+            cudaFreeAsync(d_fp, st);
+            discard(spec);
+            return fs;
         }
-        ctx->spectra.emplace(key, spec);
+        spec->key.salt = salt;
+        ctx->spectra.emplace(spec->key, spec);
     }
+    CUDA_TRY(cudaFreeAsync(d_fp, st));
     *out = spec;
     return LP_OK;
 }
@@ -589,23 +645,120 @@ extern "C" lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t d
     return LP_OK;
 }
 
+static void free_spectrum(lp_ctx* ctx, lp_spectrum* s)
+{
+    lp_ctx_free(ctx, s->data, s->bytes);
+    lp_ctx_free(ctx, s->kcopy, s->kbytes);
+    if (s->ready) cudaEventDestroy(s->ready);
+    for (int i = 0; i < lp_spectrum::kUseSlots; ++i)
+        if (s->use_event[i]) cudaEventDestroy(s->use_event[i]);
+    delete s;
+}
+
+// true when the spectrum's build and every recorded use have completed
+static bool spectrum_idle(lp_spectrum* s, bool wait)
+{
+    if (s->use_overflow) {
+        // used on more streams than it tracks: only a device-wide wait is sure
+        if (!wait) return false;
+        cudaDeviceSynchronize();
+        return true;
+    }
+    cudaEvent_t evs[1 + lp_spectrum::kUseSlots];
+    int n = 0;
+    evs[n++] = s->ready;
+    for (int i = 0; i < s->nuse; ++i) evs[n++] = s->use_event[i];
+    for (int i = 0; i < n; ++i) {
+        if (!evs[i]) continue;
+        const cudaError_t q = wait ? cudaEventSynchronize(evs[i]) : cudaEventQuery(evs[i]);
+        if (q == cudaErrorNotReady) return false;
+        if (q != cudaSuccess) cudaGetLastError();  // a failed context: nothing is running any more
+    }
+    return true;
+}
+
+void lp_reap_released(lp_ctx* ctx, bool wait)
+{
+    std::lock_guard<std::mutex> g(ctx->spec_mu);
+    if (ctx->released.empty()) return;
+    DeviceGuard dg(ctx->device);
+    std::vector<lp_spectrum*> keep;
+    for (lp_spectrum* s : ctx->released) {
+        if (spectrum_idle(s, wait)) free_spectrum(ctx, s);
+        else keep.push_back(s);
+    }
+    ctx->released.swap(keep);
+}
+
+void lp_spectrum_ref(lp_ctx* ctx, const lp_spectrum* s)
+{
+    std::lock_guard<std::mutex> g(ctx->spec_mu);
+    const_cast<lp_spectrum*>(s)->refcount++;
+}
+
+lp_status lp_spectrum_unref(lp_ctx* ctx, const lp_spectrum* cs)
+{
+    lp_spectrum* s = const_cast<lp_spectrum*>(cs);
+    {
+        std::lock_guard<std::mutex> g(ctx->spec_mu);
+        auto it = ctx->spectra.find(s->key);
+        if (it == ctx->spectra.end() || it->second != s)
+            return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: unknown spectrum");
+        if (--s->refcount > 0) return LP_OK;
+        // no new map can name it any more; maps already enqueued may still
+        // read it, so it is freed only once their use events have completed
+        ctx->spectra.erase(it);
+        ctx->released.push_back(s);
+    }
+    lp_reap_released(ctx, false);
+    return LP_OK;
+}
+
 extern "C" lp_status lp_spectrum_release(lp_ctx* ctx, lp_spectrum* s)
 {
     if (!ctx || !s) return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: NULL argument");
     if (s->ctx != ctx) return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: spectrum belongs to another context");
-    std::lock_guard<std::mutex> g(ctx->spec_mu);
-    auto it = ctx->spectra.find(s->key);
-    if (it == ctx->spectra.end() || it->second != s)
-        return lp_fail(LP_ERR_INVALID, "lp_spectrum_release: unknown spectrum");
-    if (--s->refcount == 0) {
-        DeviceGuard dg(ctx->device);
-        cudaDeviceSynchronize();  // in-flight maps may still read it
-        lp_ctx_free(ctx, s->data, s->bytes);
-        if (s->ready) cudaEventDestroy(s->ready);
-        ctx->spectra.erase(it);
-        delete s;
+    return lp_spectrum_unref(ctx, s);
+}
+
+lp_status lp_wait_spectra_built(const lp_spectrum* const* spectra, int n, cudaStream_t st)
+{
+    for (int k = 0; k < n; ++k) {
+        lp_spectrum* s = const_cast<lp_spectrum*>(spectra[k]);
+        if (s->built.load(std::memory_order_acquire)) continue;
+        const cudaError_t q = cudaEventQuery(s->ready);
+        if (q == cudaSuccess) {
+            s->built.store(true, std::memory_order_release);
+        } else if (q == cudaErrorNotReady) {
+            CUDA_TRY(cudaStreamWaitEvent(st, s->ready, 0));
+        } else {
+            return lp_fail(LP_ERR_CUDA, "spectrum build: %s", cudaGetErrorString(q));
+        }
     }
     return LP_OK;
+}
+
+void lp_note_spectra_used(lp_ctx* ctx, const lp_spectrum* const* spectra, int n, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> g(ctx->spec_mu);
+    for (int k = 0; k < n; ++k) {
+        lp_spectrum* s = const_cast<lp_spectrum*>(spectra[k]);
+        int slot = -1;
+        for (int i = 0; i < s->nuse; ++i)
+            if (s->use_stream[i] == st) slot = i;
+        if (slot < 0) {
+            if (s->nuse == lp_spectrum::kUseSlots) {
+                s->use_overflow = true;
+                continue;
+            }
+            slot = s->nuse++;
+            s->use_stream[slot] = st;
+        }
+        if (cudaEventRecord(s->use_event[slot], st) != cudaSuccess) {
+            cudaGetLastError();
+            s->use_overflow = true;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -816,6 +969,7 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     if (ps != LP_OK) return ps;
     float2* T = static_cast<float2*>(ws);
     float2* U = T + (size_t)d.ncolsT * d.ldT;
+    if ((ps = lp_wait_spectra_built(spectra, n, st)) != LP_OK) return ps;
     if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
@@ -823,6 +977,9 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         if ((ps = launch_rows_inverse(ctx, px, d, U, cnt, out + base, ldo, 0, (int)(d.ldU / 2), st)) != LP_OK)
             return ps;
     }
+    // recorded after the last pass (an event between the passes would stop
+    // the next pass's launch from overlapping the previous one's tail)
+    lp_note_spectra_used(ctx, spectra, n, st);
     return LP_OK;
 }
 
@@ -842,6 +999,7 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         if (o0 < l1 && l0 < o1) return lp_fail(LP_ERR_INVALID, "lp_map: out[%d] overlaps L", k);
     }
     DeviceGuard dg(ctx->device);
+    lp_reap_released(ctx, false);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const lp_spectrum* s0 = spectra[0];
     void* ws = nullptr;
@@ -912,7 +1070,9 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
         std::lock_guard<std::mutex> g(ctx->ws_mu);
         if (ctx->staging_bytes < need) {
             if (ctx->staging) {
-                cudaDeviceSynchronize();
+                // only the context's host-map streams touch the staging buffers
+                for (cudaStream_t hs : {ctx->hs_in, ctx->hs_comp, ctx->hs_out})
+                    if (hs) cudaStreamSynchronize(hs);
                 lp_ctx_free(ctx, ctx->staging, ctx->staging_bytes);
                 ctx->staging = nullptr;
                 ctx->staging_bytes = 0;
@@ -993,6 +1153,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
                                            ctx->hs_out));
         }
     }
+    lp_note_spectra_used(ctx, spectra, n, c);
     CUDA_TRY(cudaEventRecord(ctx->hs_ofree[obuf], ctx->hs_out));
     ctx->hs_ofree_valid[obuf] = true;
     ctx->hs_obuf = obuf ^ 1;
@@ -1004,7 +1165,8 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
 extern "C" lp_status lp_set_test_hook(lp_ctx* ctx, int hook)
 {
     if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: NULL context");
-    if (hook & ~LP_TEST_TC_NO_MMA) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: unknown hook 0x%x", hook);
+    if (hook & ~(LP_TEST_TC_NO_MMA | LP_TEST_FP_COLLIDE))
+        return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: unknown hook 0x%x", hook);
     ctx->test_hook = hook;
     return LP_OK;
 }
@@ -1027,6 +1189,7 @@ extern "C" lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms)
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    lp_reap_released(ctx, false);
     int herr = 0;
     CUDA_TRY(cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr != 0) {
@@ -1069,6 +1232,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     float2* Tb = static_cast<float2*>(ws);
     float2* U = Tb + (size_t)T * d.ncolsT * d.ldT;
     const int npairs = (int)(d.ldT / 2);
+    if ((st = lp_wait_spectra_built(spectra, T, s)) != LP_OK) return st;
     for (int t = 0; t < T; ++t) {
         P1Args a1;
         a1.L = L[t];
@@ -1132,6 +1296,7 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a3.ncols = d.ncols;
     a3.tw = px->rev;
     CUDA_TRY(px->k->p3(a3, 1, s));
+    lp_note_spectra_used(ctx, spectra, T, s);
     return LP_OK;
 }
 

@@ -50,6 +50,8 @@ bool fft64_supported(int N);
 cudaError_t psf_fingerprint_launch(const double* K, long long n, unsigned long long* d_out,
                                    cudaStream_t st);
 cudaError_t psf_symmetry_launch(const double* K, int hk, int wk, int* d_asym, cudaStream_t st);
+// *d_diff |= 1 where a[i] and b[i] differ in any bit (i < n)
+cudaError_t psf_compare_launch(const double* a, const double* b, long long n, int* d_diff, cudaStream_t st);
 cudaError_t psf_spectrum_build(const double* K, int hk, int wk, int Ny, int Nx, int real_only,
                                void* dst, long long ldK, double2* W1, double2* W1b,
                                double2* W2a, double2* W2b, cudaStream_t st);

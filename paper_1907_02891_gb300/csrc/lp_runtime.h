@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -15,9 +16,14 @@
 struct SpecKey {
     unsigned long long fp;  // order-independent fingerprint of the PSF values
     int hk, wk, ny, nx, prec;
+    int salt;  // tells apart different PSFs whose fingerprints collide
     bool operator<(const SpecKey& o) const
     {
-        return std::tie(fp, hk, wk, ny, nx, prec) < std::tie(o.fp, o.hk, o.wk, o.ny, o.nx, o.prec);
+        return std::tie(fp, hk, wk, ny, nx, prec, salt) < std::tie(o.fp, o.hk, o.wk, o.ny, o.nx, o.prec, o.salt);
+    }
+    bool same_request(const SpecKey& o) const
+    {
+        return fp == o.fp && hk == o.hk && wk == o.wk && ny == o.ny && nx == o.nx && prec == o.prec;
     }
 };
 
@@ -65,6 +71,19 @@ struct lp_spectrum {
     int refcount = 0;
     void* data = nullptr;
     cudaEvent_t ready = nullptr;  // recorded after the build on the building stream
+    std::atomic<bool> built{false};  // `ready` has been seen complete
+    // device copy of K (hk x wk FP64): a cache hit is confirmed by comparing
+    // the requested PSF with it value by value
+    double* kcopy = nullptr;
+    size_t kbytes = 0;
+    // Last use per stream, for stream-ordered release: every map call
+    // re-records the event of its stream's slot at its end.  Streams beyond
+    // the slots set `use_overflow`, and the release then waits for the device.
+    static constexpr int kUseSlots = 8;
+    cudaStream_t use_stream[kUseSlots] = {};
+    cudaEvent_t use_event[kUseSlots] = {};
+    int nuse = 0;
+    bool use_overflow = false;
 };
 
 struct lp_ctx {
@@ -73,11 +92,14 @@ struct lp_ctx {
     std::mutex mem_mu, plan_mu, spec_mu, ws_mu;
     std::map<int, std::unique_ptr<PlanRec>> plans;
     std::map<SpecKey, lp_spectrum*> spectra;
+    // released spectra whose last uses may still be running: freed once
+    // their build and use events have completed
+    std::vector<lp_spectrum*> released;
     std::vector<Workspace> ws;
     void* staging = nullptr;
     size_t staging_bytes = 0;
     int* d_err = nullptr;  // sticky device status word
-    int test_hook = 0;     // lp_set_test_hook
+    int test_hook = 0;     // lp_set_test_hook bits
     ServeState* serve = nullptr;
     // pass timing
     std::mutex tim_mu;
@@ -110,6 +132,17 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                         const MapDims& d, void* ws, cudaStream_t st);
 void lp_serve_shutdown(lp_ctx* ctx);
+// Map calls wait, in stream order, for the builds of their spectra that are
+// not yet known to be complete (no wait once a build has been seen done).
+lp_status lp_wait_spectra_built(const lp_spectrum* const* spectra, int n, cudaStream_t st);
+// Records the end of a map call on stream st as the last use of each spectrum.
+void lp_note_spectra_used(lp_ctx* ctx, const lp_spectrum* const* spectra, int n, cudaStream_t st);
+// Reference counting shared by lp_spectrum_release and the request scheduler
+// (which holds one reference per queued or running request).
+void lp_spectrum_ref(lp_ctx* ctx, const lp_spectrum* s);
+lp_status lp_spectrum_unref(lp_ctx* ctx, const lp_spectrum* s);
+// Frees released spectra whose last uses are complete; wait = block for them.
+void lp_reap_released(lp_ctx* ctx, bool wait);
 // records the start of pass `pass` on stream s when timing is on; returns a
 // token for lp_pass_end (-1 when off)
 int lp_pass_begin(lp_ctx* ctx, int pass, cudaStream_t s);

@@ -44,6 +44,7 @@ struct Slot {
     bool busy = false;
     uint64_t ticket = 0;
     size_t footprint = 0;
+    std::vector<const lp_spectrum*> spectra;  // references held by the running request
     Clock::time_point submitted, started;
 };
 
@@ -78,6 +79,8 @@ struct ServeState {
 static void finish_slot(ServeState* S, Slot& sl, lp_status st)
 {
     const auto now = Clock::now();
+    for (const lp_spectrum* sp : sl.spectra) lp_spectrum_unref(S->ctx, sp);
+    sl.spectra.clear();
     Result r;
     r.status = st;
     r.latency_ms = std::chrono::duration<double, std::milli>(now - sl.submitted).count();
@@ -128,6 +131,7 @@ static void scheduler_loop(ServeState* S)
                 st = lp_launch_map(S->ctx, rq.L, rq.h, rq.w, rq.ldl, rq.spectra.data(), (int)rq.spectra.size(),
                                    rq.out.data(), rq.ldo, rq.dims, ws, sl.stream);
             sl.ticket = rq.ticket;
+            sl.spectra = rq.spectra;
             sl.submitted = rq.submitted;
             sl.started = Clock::now();
             sl.footprint = rq.footprint;
@@ -198,8 +202,9 @@ extern "C" lp_status lp_serve_submit(lp_ctx* ctx, const float* L, int h, int w, 
     if (!ctx || !ticket) return lp_fail(LP_ERR_INVALID, "lp_serve_submit: NULL argument");
     ServeState* S = ctx->serve;
     if (!S) return lp_fail(LP_ERR_BUSY, "lp_serve_submit: serving not started");
+    if (!spectra || n < 1 || !spectra[0]) return lp_fail(LP_ERR_INVALID, "lp_serve_submit: need spectra");
     MapDims d;
-    lp_status st = lp_validate_map(ctx, L, h, w, ldl, spectra, n, out, ldo, mode, LP_PREC_FP32, &d);
+    lp_status st = lp_validate_map(ctx, L, h, w, ldl, spectra, n, out, ldo, mode, spectra[0]->prec, &d);
     if (st != LP_OK) return st;
     for (int k = 0; k < n; ++k)
         if (!out[k]) return lp_fail(LP_ERR_INVALID, "lp_serve_submit: out[%d] is NULL", k);
@@ -224,6 +229,7 @@ extern "C" lp_status lp_serve_submit(lp_ctx* ctx, const float* L, int h, int w, 
                            rq.footprint, S->capacity);
         rq.ticket = S->next_ticket++;
         *ticket = rq.ticket;
+        for (const lp_spectrum* sp : rq.spectra) lp_spectrum_ref(ctx, sp);
         S->queue.push_back(std::move(rq));
     }
     S->cv_work.notify_one();

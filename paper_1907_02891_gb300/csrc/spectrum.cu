@@ -174,7 +174,10 @@ __global__ void psf_store_spectrum(const double2* __restrict__ W2, int Ny, int n
     }
 }
 
-// order-independent 64-bit fingerprint of the PSF values (cache key)
+// order-independent 64-bit fingerprint of the PSF values (cache key).  mix64
+// is the SplitMix64 output finaliser (Steele, Lea and Flood, "Fast
+// splittable pseudorandom number generators", OOPSLA 2014): its published
+// shift and multiplier constants, applied to value bits and index.
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
     z += 0x9E3779B97F4A7C15ull;
@@ -196,6 +199,20 @@ cudaError_t psf_fingerprint_launch(const double* K, long long n, unsigned long l
 {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     psf_fingerprint<<<blocks, 256, 0, st>>>(K, n, d_out);
+    return cudaGetLastError();
+}
+
+__global__ void psf_compare(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                            int* diff)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (__double_as_longlong(a[i]) != __double_as_longlong(b[i])) atomicOr(diff, 1);
+}
+
+cudaError_t psf_compare_launch(const double* a, const double* b, long long n, int* d_diff, cudaStream_t st)
+{
+    psf_compare<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n, d_diff);
     return cudaGetLastError();
 }
 

@@ -263,6 +263,7 @@ PASS_NAMES = ("p1_rows", "p2_cols", "p3_rows")
 
 
 LP_TEST_TC_NO_MMA = 1
+LP_TEST_FP_COLLIDE = 2
 
 
 def lp_set_test_hook(ctx: int, hook: int) -> None:
@@ -314,8 +315,9 @@ def lp_serve_start(ctx: int, n_slots: int = 4) -> None:
 
 def lp_serve_submit(ctx: int, L, spectra: Sequence[int], out: Sequence,
                     mode: int = LP_OUT_SAME) -> int:
-    """Queue one map request (device tensors, as lp_map); returns its ticket.
-    Keep L, the spectra and out alive until the ticket is polled."""
+    """Queue one map request (device tensors, as lp_map; the precision is the
+    spectra's); returns its ticket.  Keep L and out alive until the ticket is
+    polled (the request holds its own references on the spectra)."""
     h, w = L.shape
     ldo = out[0].stride(0)
     t = ctypes.c_uint64()

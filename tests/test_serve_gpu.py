@@ -131,3 +131,80 @@ def test_serving_errors_and_bounded_poll():
         lp.lp_serve_stop(ctx)
     finally:
         lp.lp_destroy(ctx)
+
+
+def test_split_precision_requests_same_alone_and_in_the_mix():
+    """The scheduler runs split-BF16 spectra too (the request takes the
+    spectra's precision); results equal lp_map's bitwise."""
+    ctx = lp.lp_create(0)
+    try:
+        sides = (256, 512)
+        Ks = [synth.psf_power_exp(31, 0.742, 0.1, p, lam) for (p, lam) in [(1.25, 40.0), (2.0, 80.0)]]
+        spectra = {(s, i): lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(DEV), max_h=s, max_w=s,
+                                                 prec=lp.LP_PREC_SPLIT_BF16)
+                   for s in sides for i, K in enumerate(Ks)}
+        reqs = []
+        for r in range(12):
+            s = sides[r % 2]
+            ks = [0, 1] if r % 3 == 0 else [r % 2]
+            reqs.append((s, ks, torch.from_numpy(synth.radiance_map(s, s, 6, 700 + r)).to(DEV)))
+        alone = []
+        for s, ks, L in reqs:
+            outs = [torch.empty((s, s), device=DEV) for _ in ks]
+            lp.lp_map(ctx, L, [spectra[(s, i)] for i in ks], outs, prec=lp.LP_PREC_SPLIT_BF16)
+            alone.append(outs)
+        lp.lp_sync_status(ctx)
+        lp.lp_serve_start(ctx, 3)
+        mixed, tickets = [], []
+        for s, ks, L in reqs:
+            outs = [torch.full((s, s), float("nan"), device=DEV) for _ in ks]
+            tickets.append(lp.lp_serve_submit(ctx, L, [spectra[(s, i)] for i in ks], outs))
+            mixed.append(outs)
+        for t in tickets:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+        lp.lp_serve_stop(ctx)
+        for a, b in zip(alone, mixed):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        s, ks, L = reqs[1]
+        ref = oracle.conv_same(L.cpu().numpy(), Ks[ks[0]])
+        got = mixed[1][0].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 2e-4
+    finally:
+        lp.lp_destroy(ctx)
+
+
+def test_release_mid_run_does_not_stall_the_slots():
+    """Spectra released while requests are queued or running: the requests
+    hold their own references, so they finish with correct results; a
+    spectrum whose last use has completed is freed at once; no release
+    waits for the device, so the slots are still busy right after it."""
+    ctx = lp.lp_create(0)
+    try:
+        Ks, spectra = _bank(ctx, (8192, 256), n_psf=4, psf_side=201)
+        L = torch.from_numpy(synth.radiance_map(8192, 8192, 1600, 9)).to(DEV)
+        ref = [torch.empty((8192, 8192), device=DEV) for _ in range(4)]
+        lp.lp_map(ctx, L, [spectra[(8192, i)] for i in range(4)], ref)
+        lp.lp_sync_status(ctx)
+        lp.lp_serve_start(ctx, 2)
+        # size both slots' workspaces first, so that nothing else allocates below
+        wouts = [[torch.empty((8192, 8192), device=DEV) for _ in range(4)] for _ in range(2)]
+        warm = [lp.lp_serve_submit(ctx, L, [spectra[(8192, i)] for i in range(4)], w) for w in wouts]
+        for t in warm:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+        outs = [[torch.full((8192, 8192), float("nan"), device=DEV) for _ in range(4)] for _ in range(4)]
+        tickets = [lp.lp_serve_submit(ctx, L, [spectra[(8192, i)] for i in range(4)], o) for o in outs]
+        for i in range(4):                      # drop the caller's references
+            lp.lp_spectrum_release(ctx, spectra[(8192, i)])
+        held = lp.lp_bytes_in_use(ctx)
+        lp.lp_spectrum_release(ctx, spectra[(256, 0)])   # unused by the queue: freed at once
+        assert lp.lp_serve_poll(ctx, tickets[-1], timeout_ms=0) is None, "a release waited for the device"
+        assert lp.lp_bytes_in_use(ctx) < held
+        for t in tickets:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+        lp.lp_serve_stop(ctx)
+        for o in outs:
+            for x, y in zip(o, ref):
+                assert torch.equal(x, y)
+    finally:
+        lp.lp_destroy(ctx)

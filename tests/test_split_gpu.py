@@ -123,7 +123,7 @@ def test_split_map8192_psf601x16_sampled(ctx):
     L, Ks = wl.radiance(), wl.psfs()
     Bs = run_split(ctx, L, Ks)
     for k, (K, B) in enumerate(zip(Ks, Bs)):
-        assert _sampled_check(L, K, B, wl.seed + 200 + k, n=256, top=16) <= TOL_SPLIT, k
+        assert _sampled_check(L, K, B, wl.seed + 200 + k) <= TOL_SPLIT, k
 
 
 def test_split_map16384_psf801_sampled(ctx):
