@@ -473,9 +473,11 @@ def test_release_is_stream_ordered(ctx):
         spec = lp.lp_kernel_spectrum(c2, K, max_h=8192, max_w=8192)
         ref = torch.empty((8192, 8192), device=DEV)
         lp.lp_map(c2, L, [spec], [ref])
-        lp.lp_sync_status(c2)
-        held = lp.lp_bytes_in_use(c2)
         side = torch.cuda.Stream()
+        lp.lp_map(c2, L, [spec], [ref], stream=side)     # the side stream's workspace
+        lp.lp_sync_status(c2)
+        lp.lp_sync_status(c2, stream=side)
+        held = lp.lp_bytes_in_use(c2)
         outs = [torch.full((8192, 8192), float("nan"), device=DEV) for _ in range(6)]
         for o in outs:
             lp.lp_map(c2, L, [spec], [o], stream=side)
