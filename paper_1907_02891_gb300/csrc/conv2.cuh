@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
     ip_forward<G, 1, G::S - 1, T, C>(X, t, a.tw);
     // the forward's last stage, parked (each thread later reads back only
     // the elements it wrote, so no barrier is needed around the park)
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int blk = t + e * T;
         if (NB % T != 0 && blk >= NB) break;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
         const void *k0, *k1;
         unit_spectra<C, KREAL>(a, s, unit, k0, k1);
         __syncthreads();  // the previous spectrum's last stage has read X
-#pragma unroll
+#pragma unroll 1
         for (int e = 0; e < E; ++e) {
             const int blk = t + e * T;
             if (NB % T != 0 && blk >= NB) break;
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multiclass(const __grid_constant
         const void *k0, *k1;
         unit_spectra<C, KREAL>(a, q, unit, k0, k1);
         // each thread accumulates only the elements it owns
-#pragma unroll
+#pragma unroll 1
         for (int e = 0; e < E; ++e) {
             const int blk = t + e * T;
             if (NB % T != 0 && blk >= NB) break;
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multiclass(const __grid_constant
         }
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int blk = t + e * T;
         if (NB % T != 0 && blk >= NB) break;

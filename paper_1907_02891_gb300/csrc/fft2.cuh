@@ -39,6 +39,7 @@
 #pragma once
 
 #include "fft_core.cuh"
+#include "lp_internal.h"
 
 namespace lpk {
 
@@ -262,10 +263,7 @@ template <int R, int DIR, class C> struct D2 {
 // exp(-i 2 pi j k / B_s), 1 <= k < R_s, j < D_s, stored as float4
 // {cos, cos, sin, sin} (the value and its pair form for two transforms).
 // ---------------------------------------------------------------------------
-struct TwTab2 {
-    const float4* p[8];
-    const unsigned short* pos;  // frequency -> position after the forward transform (N entries)
-};
+// (TwTab2, lp_internal.h: the per-stage tables and the position table)
 
 // v *= w (DIR < 0, the forward twiddle) or v *= conj(w) (DIR > 0)
 template <int DIR>
@@ -348,7 +346,7 @@ __device__ __forceinline__ void ip_stage(C* X, int t, const TwTab2& tw)
 {
     constexpr int R = G::r(s), Ds = G::D(s), NB = G::B(0) / R;
     constexpr int E = (NB + T - 1) / T;
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int b = t + e * T;
         if (NB % T != 0 && b >= NB) break;
@@ -406,7 +404,7 @@ __device__ __forceinline__ void ip_first_forward(C* X, int t, const TwTab2& tw, 
     constexpr int R = G::R0, Ds = G::D(0), NB = G::B(0) / R;
     constexpr int E = (NB + T - 1) / T;
     static_assert(G::jfast(0) || Ds == 1, "stage 0 visits consecutive j");
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int b = t + e * T;
         if (NB % T != 0 && b >= NB) break;
@@ -432,7 +430,7 @@ __device__ __forceinline__ void ip_last_inverse(const C* X, int t, const TwTab2&
 {
     constexpr int R = G::R0, Ds = G::D(0), NB = G::B(0) / R;
     constexpr int E = (NB + T - 1) / T;
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int b = t + e * T;
         if (NB % T != 0 && b >= NB) break;
@@ -459,7 +457,7 @@ __device__ __forceinline__ void ip_middle(C* X, int t, Op&& op)
 {
     constexpr int R = G::RL, NB = G::B(0) / R, FS = G::B(0) / R;  // frequency step
     constexpr int E = (NB + T - 1) / T;
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
         const int blk = t + e * T;
         if (NB % T != 0 && blk >= NB) break;

@@ -13,29 +13,41 @@ struct TwChain {
     const float2* p[6];
 };
 
-struct P1Args;
 struct P2Args;
-struct P3Args;
-struct P2MArgs;
 struct P2TcArgs;
+struct P1v2Args;
+struct P2v2Args;
+struct P3v2Args;
+struct P2Mv2Args;
 
-// One supported FFT length with its compiled FP32 kernels.
+// Tables of the in-place engine (fft2.cuh) for one length: per stage s < S-1
+// the twiddles exp(-i 2 pi j k / B_s) at [(k-1) D_s + j] as float4
+// {cos, cos, sin, sin} (value and two-transform pair form), and the position
+// of every frequency after the forward transform.
+struct TwTab2 {
+    const float4* p[8];
+    const unsigned short* pos;
+};
+
+// One supported FFT length with its compiled kernels.
 struct SizeKernels {
     int N;
+    // FP32 passes on the in-place engine
     int nstages;
-    int radices[6];      // forward order
-    int threads;         // threads per transform
-    int f1, f3;          // transforms per block in the row passes
-    int smem_bytes;      // dynamic shared memory of one transform
+    int radices[8];   // forward (DIF) order
+    int pair[3];      // two transforms per block in P1, P2, P3
+    int threads[3];
+    int batch;        // several spectra: one forward column transform for all
     cudaError_t (*set_attrs)();
-    // launchers: pick the persistent prefetching kernel when its shared
-    // memory fits, the one-unit-per-block kernel otherwise
-    cudaError_t (*p1)(const P1Args&, cudaStream_t);
-    cudaError_t (*p2)(const P2Args&, bool kreal, cudaStream_t);
-    cudaError_t (*p2m)(const P2MArgs&, bool kreal, cudaStream_t);
-    cudaError_t (*p3)(const P3Args&, int nspec, cudaStream_t);
+    cudaError_t (*p1)(const P1v2Args&, cudaStream_t);
+    cudaError_t (*p2)(const P2v2Args&, bool kreal, cudaStream_t);
+    cudaError_t (*p2m)(const P2Mv2Args&, bool kreal, cudaStream_t);
+    cudaError_t (*p3)(const P3v2Args&, int nspec, cudaStream_t);
     // split-precision (BF16 hi/lo) tensor-core column pass, one spectrum per
-    // launch; tc_smem = 0 where this length has none
+    // launch, on its own Stockham radix plan; tc_smem = 0 where this length
+    // has none
+    int tc_nstages;
+    int tc_radices[6];
     int tc_threads;
     int tc_smem;
     cudaError_t (*p2tc)(const P2TcArgs&, bool kreal, cudaStream_t);
