@@ -266,32 +266,14 @@ static void fill_tc_steps(const int* r, int ns, int dir, float2* dst)
     }
 }
 
-// Tables of the in-place engine for one plan (radices rs[0..ns) in DIF
-// order): per stage s < ns-1 the twiddles exp(-i 2 pi j k / B_s) at
-// [(k-1) D_s + j] as {cos, cos, sin, sin}, computed in FP64; offs[s] = the
-// stage's first entry.  Returns the entry count.
-static size_t fill_ip_tables(int N, const int* rs, int ns, std::vector<float4>* host, size_t* offs)
+// Twiddles of the in-place engine: W[i] = exp(-i 2 pi i / N), i < N, as
+// {cos, sin}, computed in FP64.
+static void fill_ip_twiddles(int N, float2* w)
 {
-    size_t tot = 0;
-    long B = N;
-    for (int s = 0; s < ns; ++s) {
-        const long D = B / rs[s];
-        offs[s] = tot;
-        if (s < ns - 1) {
-            for (int k = 1; k < rs[s]; ++k)
-                for (long j = 0; j < D; ++j) {
-                    if (host) {
-                        const long t = (j * k) % B;
-                        const double th = 2.0 * M_PI * (double)t / (double)B;
-                        const float c = (float)std::cos(th), sn = (float)-std::sin(th);
-                        (*host)[tot + (size_t)(k - 1) * D + j] = make_float4(c, c, sn, sn);
-                    }
-                }
-            tot += (size_t)(rs[s] - 1) * D;
-        }
-        B = D;
+    for (long i = 0; i < N; ++i) {
+        const double th = 2.0 * M_PI * (double)i / (double)N;
+        w[i] = make_float2((float)std::cos(th), (float)-std::sin(th));
     }
-    return tot;
 }
 
 // position of every frequency after the in-place forward transform:
@@ -322,12 +304,10 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     const SizeKernels* k = find_size(N);
     if (!k) return lp_fail(LP_ERR_UNSUPPORTED, "FFT length %d is not built into this library", N);
     if (N > 65535) return lp_fail(LP_ERR_UNSUPPORTED, "FFT length %d exceeds the position table", N);
-    // one device block: in-place engine twiddles (float4), positions
+    // one device block: in-place engine twiddles (float2), positions
     // (uint16), then the tensor-core pass's Stockham twiddles (float2) and,
     // 256-byte aligned, its split-BF16 DFT matrices and step factors
-    size_t ipoff[8] = {0};
-    const size_t nip = fill_ip_tables(N, k->radices, k->nstages, nullptr, ipoff);
-    const size_t pos_off = (nip * sizeof(float4) + 15) / 16 * 16;
+    const size_t pos_off = ((size_t)N * sizeof(float2) + 15) / 16 * 16;
     const size_t chain_off = (pos_off + (size_t)N * sizeof(uint16_t) + 15) / 16 * 16;
     int fwd[6], rev[6];
     const int ns = k->tc_nstages;
@@ -346,12 +326,8 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     const size_t tsr = k->tc_smem > 0 ? tc_step_bytes(rev, ns) : 0;
     const size_t total = k->tc_smem > 0 ? tc_off + (tcf + tsf + tsr + 15) / 16 * 16 : tw_end;
     std::vector<unsigned char> host(total, 0);
-    {
-        std::vector<float4> ipt(nip + 1);
-        fill_ip_tables(N, k->radices, k->nstages, &ipt, ipoff);
-        std::memcpy(host.data(), ipt.data(), nip * sizeof(float4));
-        fill_ip_positions(N, k->radices, k->nstages, reinterpret_cast<uint16_t*>(host.data() + pos_off));
-    }
+    fill_ip_twiddles(N, reinterpret_cast<float2*>(host.data()));
+    fill_ip_positions(N, k->radices, k->nstages, reinterpret_cast<uint16_t*>(host.data() + pos_off));
     std::vector<float2> tw(nf + nr + 1);
     size_t of[6] = {0}, orv[6] = {0};
     fill_chain_tables(fwd, ns, tw, 0, of);
@@ -375,8 +351,7 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
         return lp_fail(LP_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e));
     }
     char* base = static_cast<char*>(d);
-    for (int s = 0; s < 8; ++s)
-        rec->ip.p[s] = (s < k->nstages - 1) ? reinterpret_cast<const float4*>(base) + ipoff[s] : nullptr;
+    rec->ip.w = reinterpret_cast<const float2*>(base);
     rec->ip.pos = reinterpret_cast<const unsigned short*>(base + pos_off);
     float2* chain = reinterpret_cast<float2*>(base + chain_off);
     for (int s = 0; s < 6; ++s) {
@@ -532,8 +507,8 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     }
     // plans used later by lp_map (allocating here keeps lp_map allocation-free
     // once its workspace exists)
-    const PlanRec* pr;
-    lp_status s0 = lp_get_plan(ctx, Ny, &pr);
+    const PlanRec *pr, *pry;
+    lp_status s0 = lp_get_plan(ctx, Ny, &pry);
     if (s0 != LP_OK) return s0;
     s0 = lp_get_plan(ctx, Nx, &pr);
     if (s0 != LP_OK) return s0;
@@ -593,9 +568,12 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
             return LP_OK;
         }
     }
+    // FP32: the column pass's layout (column pairs in position order);
+    // split precision: natural layout, one row per column-frequency
     const int ncols = Nx / 2 + 1;
     const long long ldK = ((long long)Ny + 31) / 32 * 32;
-    const size_t bytes = (size_t)ncols * ldK * (is_real ? 4 : 8);
+    const size_t bytes = split ? (size_t)ncols * ldK * (is_real ? 4 : 8)
+                               : (size_t)pair_count(ncols) * ldK * (is_real ? 8 : 16);
     auto spec = new (std::nothrow) lp_spectrum();
     if (!spec) {
         cudaFreeAsync(d_fp, st);
@@ -647,7 +625,7 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     if (e == cudaSuccess)
         e = psf_spectrum_build(K, hk, wk, Ny, Nx, is_real, dptr, ldK, (double2*)scratch,
                                (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
-                               (double2*)(scratch + 2 * w1 + w2), st);
+                               (double2*)(scratch + 2 * w1 + w2), split ? nullptr : pry->ip.pos, st);
     cudaFreeAsync(scratch, st);
     for (int i = 0; e == cudaSuccess && i < lp_spectrum::kUseSlots; ++i)
         e = cudaEventCreateWithFlags(&spec->use_event[i], cudaEventDisableTiming);
@@ -701,6 +679,15 @@ extern "C" lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t d
         return lp_fail(LP_ERR_INVALID, "lp_spectrum_copy: destination holds %zu floats, need %zu",
                        dst_floats, ncols * s->ny * per);
     DeviceGuard dg(s->ctx->device);
+    if (s->prec == LP_PREC_FP32) {
+        // stored in the column pass's layout: gather back to natural order
+        const PlanRec* py;
+        lp_status st = lp_get_plan(s->ctx, s->ny, &py);
+        if (st != LP_OK) return st;
+        CUDA_TRY(psf_copy_natural_launch(s->data, s->ny, (int)ncols, s->ldK, s->is_real, py->ip.pos, dst,
+                                         static_cast<cudaStream_t>(stream)));
+        return LP_OK;
+    }
     CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)s->ny * per * 4, s->data, (size_t)s->ldK * per * 4,
                                (size_t)s->ny * per * 4, ncols, cudaMemcpyDeviceToDevice,
                                static_cast<cudaStream_t>(stream)));

@@ -29,6 +29,14 @@
 // column pair and row (64 contiguous bytes for the four rows of a
 // two-transform block).  The column past the last one (odd Nx/2 + 1) is
 // written by P1 and never read.
+//
+// FP32 PSF spectra are stored for the column pass: per column pair q, Ny
+// entries (leading dimension ldK) in the position order of the column
+// transform (entry p holds the frequency the forward transform leaves at
+// position p), each {K[2q], K[2q+1]} (real spectrum) or {re K[2q], re K[2q+1],
+// im K[2q], im K[2q+1]} (complex spectrum).  The product then reads the
+// spectrum in the order the transform holds its values: contiguous per
+// butterfly, coalesced across the threads.
 #pragma once
 
 #include "conv_kernels.cuh"
@@ -121,28 +129,27 @@ __global__ void __launch_bounds__(T, MINB) p1v2(const P1v2Args a)
     constexpr int ROWS = PAIR ? 4 : 2;  // map rows per block
     extern __shared__ float4 smem_v2[];
     C* X = reinterpret_cast<C*>(smem_v2);
+    float* Xf = reinterpret_cast<float*>(smem_v2);
     const int t = threadIdx.x;
     const int unit = a.unit0 + blockIdx.x;
     const int r0 = ROWS * unit;
-    const float* Lr[ROWS];
-    bool ok[ROWS];
+    // element n of the packed transforms: rows (a_A, a_B, b_A, b_B) of column
+    // n for two transforms, (a, b) for one; columns >= W and rows >= H are 0
+    constexpr int SLOT[4] = {0, 2, 1, 3};  // map row i -> float of the element
+    for (int n = t; n < N; n += T) {
 #pragma unroll
-    for (int i = 0; i < ROWS; ++i) {
-        ok[i] = r0 + i < a.H;
-        Lr[i] = a.L + (long long)(ok[i] ? r0 + i : 0) * a.ldl;
+        for (int i = 0; i < ROWS; ++i) {
+            float* dst = Xf + (size_t)n * ROWS + (PAIR ? SLOT[i] : i);
+            if (n < a.W && r0 + i < a.H) cpa4(dst, a.L + (long long)(r0 + i) * a.ldl + n);
+            else *dst = 0.f;
+        }
     }
-    ip_first_forward<G, T, C>(X, t, a.tw, [&](int col) -> C {
-        const bool in = col < a.W;
-        float v[ROWS];
-#pragma unroll
-        for (int i = 0; i < ROWS; ++i) v[i] = (in && ok[i]) ? __ldg(Lr[i] + col) : 0.f;
-        if constexpr (PAIR) return CP{make_float2(v[0], v[2]), make_float2(v[1], v[3])};
-        else return make_float2(v[0], v[1]);
-    });
+    cpa_wait_all();
     __syncthreads();
-    ip_forward<G, 1, G::S, T, C>(X, t, a.tw);
+    ip_forward<G, 0, G::S, T, C>(X, t, a.tw);
     // half spectra of the block's rows, by column pair
     const int ncp = (int)pair_count(a.ncols);
+#pragma unroll 2
     for (int q = t; q < ncp; q += T) {
         C xa[2], xb[2];
 #pragma unroll
@@ -170,32 +177,45 @@ __global__ void __launch_bounds__(T, MINB) p1v2(const P1v2Args a)
 // ---------------------------------------------------------------------------
 // P2: column transform with the spectrum product
 // ---------------------------------------------------------------------------
-// spectrum value(s) of frequency f for the unit's column(s)
+// The unit's spectrum in the column-pass layout (position order): the pair
+// q's entries (two transforms) or column c's lane of them (one transform).
+template <class C, bool KREAL>
+struct SpecIo;
 template <bool KREAL>
-__device__ __forceinline__ void product(CP& v, const void* k0, const void* k1, int f)
-{
-    if constexpr (KREAL) {
-        const float2 kk = make_float2(__ldg(static_cast<const float*>(k0) + f), __ldg(static_cast<const float*>(k1) + f));
-        v.x = mul2(v.x, kk);
-        v.y = mul2(v.y, kk);
-    } else {
-        const float2 a = __ldg(static_cast<const float2*>(k0) + f), b = __ldg(static_cast<const float2*>(k1) + f);
-        const float2 kr = make_float2(a.x, b.x), ki = make_float2(a.y, b.y);
-        const CP r{fma2(v.y, neg2(ki), mul2(v.x, kr)), fma2(v.x, ki, mul2(v.y, kr))};
-        v = r;
+struct SpecIo<CP, KREAL> {
+    const char* base;
+    __device__ __forceinline__ SpecIo(const void* K, long long ldK, int unit)
+        : base(static_cast<const char*>(K) + (size_t)unit * ldK * (KREAL ? 8 : 16)) {}
+    __device__ __forceinline__ void apply(CP& v, int p) const
+    {
+        if constexpr (KREAL) {
+            const float2 kk = __ldg(reinterpret_cast<const float2*>(base) + p);
+            v.x = mul2(v.x, kk);
+            v.y = mul2(v.y, kk);
+        } else {
+            const float4 k4 = __ldg(reinterpret_cast<const float4*>(base) + p);
+            const float2 kr = make_float2(k4.x, k4.y), ki = make_float2(k4.z, k4.w);
+            const CP r{fma2(v.y, neg2(ki), mul2(v.x, kr)), fma2(v.x, ki, mul2(v.y, kr))};
+            v = r;
+        }
     }
-}
+};
 template <bool KREAL>
-__device__ __forceinline__ void product(float2& v, const void* k0, const void*, int f)
-{
-    if constexpr (KREAL) {
-        const float k = __ldg(static_cast<const float*>(k0) + f);
-        v = make_float2(v.x * k, v.y * k);
-    } else {
-        const float2 k = __ldg(static_cast<const float2*>(k0) + f);
-        v = make_float2(v.x * k.x - v.y * k.y, v.x * k.y + v.y * k.x);
+struct SpecIo<float2, KREAL> {
+    const float* base;
+    __device__ __forceinline__ SpecIo(const void* K, long long ldK, int c)
+        : base(static_cast<const float*>(K) + (size_t)(c >> 1) * ldK * (KREAL ? 2 : 4) + (c & 1)) {}
+    __device__ __forceinline__ void apply(float2& v, int p) const
+    {
+        if constexpr (KREAL) {
+            const float k = __ldg(base + 2 * p);
+            v = make_float2(v.x * k, v.y * k);
+        } else {
+            const float kr = __ldg(base + 4 * p), ki = __ldg(base + 4 * p + 2);
+            v = make_float2(v.x * kr - v.y * ki, v.x * ki + v.y * kr);
+        }
     }
-}
+};
 
 // The unit's column data: pair q (CP) or column c (float2: lane c & 1).
 template <class C>
@@ -206,7 +226,7 @@ struct ColIo<CP> {
     float4* dst;
     __device__ __forceinline__ ColIo(const float4* T, long long ldT, float4* U, long long ldU, int unit)
         : src(T + (long long)unit * ldT), dst(U + (long long)unit * ldU) {}
-    __device__ __forceinline__ CP load(int r) const { return cp_of(ldg4(src + r)); }
+    __device__ __forceinline__ void stage(CP* X, int r) const { cpa16(X + r, src + r); }
     __device__ __forceinline__ void store(int r, const CP& v) const { dst[r] = f4_of(v); }
 };
 template <>
@@ -216,7 +236,11 @@ struct ColIo<float2> {
     __device__ __forceinline__ ColIo(const float4* T, long long ldT, float4* U, long long ldU, int c)
         : src(reinterpret_cast<const float*>(T + (long long)(c >> 1) * ldT) + (c & 1)),
           dst(reinterpret_cast<float*>(U + (long long)(c >> 1) * ldU) + (c & 1)) {}
-    __device__ __forceinline__ float2 load(int r) const { return make_float2(__ldg(src + 4 * r), __ldg(src + 4 * r + 2)); }
+    __device__ __forceinline__ void stage(float2* X, int r) const
+    {
+        cpa4(reinterpret_cast<float*>(X + r), src + 4 * r);
+        cpa4(reinterpret_cast<float*>(X + r) + 1, src + 4 * r + 2);
+    }
     __device__ __forceinline__ void store(int r, const float2& v) const
     {
         dst[4 * r] = v.x;
@@ -231,19 +255,16 @@ __device__ __forceinline__ C czero()
     else return make_float2(0.f, 0.f);
 }
 
-// spectrum rows of the unit's columns (the second one clamped for an odd count)
-template <class C, bool KREAL>
-__device__ __forceinline__ void unit_spectra(const P2v2Args& a, int s, int unit, const void*& k0, const void*& k1)
+// the column (pair) rows [0, H) staged into X, zeros up to N
+template <int N, int T, class C>
+__device__ __forceinline__ void stage_column(C* X, const ColIo<C>& io, int H, int t)
 {
-    const size_t w = KREAL ? 4 : 8;
-    const char* base = static_cast<const char*>(a.K[s]);
-    if constexpr (std::is_same<C, CP>::value) {
-        const int c0 = 2 * unit, c1 = (2 * unit + 1 < a.ncols) ? 2 * unit + 1 : 2 * unit;
-        k0 = base + (size_t)c0 * a.ldK * w;
-        k1 = base + (size_t)c1 * a.ldK * w;
-    } else {
-        k0 = k1 = base + (size_t)unit * a.ldK * w;
+    for (int r = t; r < N; r += T) {
+        if (r < H) io.stage(X, r);
+        else X[r] = czero<C>();
     }
+    cpa_wait_all();
+    __syncthreads();
 }
 
 template <class G, int T, int MINB, class C, bool KREAL>
@@ -256,12 +277,10 @@ __global__ void __launch_bounds__(T, MINB) p2v2(const __grid_constant__ P2v2Args
     const int t = threadIdx.x;
     const int unit = blockIdx.x;
     const ColIo<C> io(a.T, a.ldT, a.U, a.ldU, unit);
-    ip_first_forward<G, T, C>(X, t, a.tw, [&](int r) -> C { return r < a.H ? io.load(r) : czero<C>(); });
-    __syncthreads();
-    ip_forward<G, 1, G::S - 1, T, C>(X, t, a.tw);
-    const void *k0, *k1;
-    unit_spectra<C, KREAL>(a, 0, unit, k0, k1);
-    ip_middle<G, T, C>(X, t, [&](int, int f, C& v) { product<KREAL>(v, k0, k1, f); });
+    stage_column<N, T, C>(X, io, a.H, t);
+    ip_forward<G, 0, G::S - 1, T, C>(X, t, a.tw);
+    const SpecIo<C, KREAL> sp(a.K[0], a.ldK, unit);
+    ip_middle<G, T, C>(X, t, [&](int p, C& v) { sp.apply(v, p); });
     __syncthreads();
     ip_inverse<G, 1, G::S - 1, T, C>(X, t, a.tw);
     ip_last_inverse<G, T, C>(X, t, a.tw, [&](int n, const C& v) {
@@ -280,7 +299,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
 {
     pdl_begin();
     constexpr int N = G::B(0);
-    constexpr int R = G::RL, NB = N / R, FS = N / R;
+    constexpr int R = G::RL, NB = N / R;
     constexpr int E = (NB + T - 1) / T;
     extern __shared__ float4 smem_v2[];
     C* X = reinterpret_cast<C*>(smem_v2);
@@ -288,9 +307,8 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
     const int t = threadIdx.x;
     const int unit = blockIdx.x;
     const ColIo<C> io(a.T, a.ldT, a.U, a.ldU, unit);
-    ip_first_forward<G, T, C>(X, t, a.tw, [&](int r) -> C { return r < a.H ? io.load(r) : czero<C>(); });
-    __syncthreads();
-    ip_forward<G, 1, G::S - 1, T, C>(X, t, a.tw);
+    stage_column<N, T, C>(X, io, a.H, t);
+    ip_forward<G, 0, G::S - 1, T, C>(X, t, a.tw);
     // the forward's last stage, parked (each thread later reads back only
     // the elements it wrote, so no barrier is needed around the park)
 #pragma unroll 1
@@ -305,8 +323,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
         for (int k = 0; k < R; ++k) park[blk * R + k] = v[k];
     }
     for (int s = 0; s < a.nspec; ++s) {
-        const void *k0, *k1;
-        unit_spectra<C, KREAL>(a, s, unit, k0, k1);
+        const SpecIo<C, KREAL> sp(a.K[s], a.ldK, unit);
         __syncthreads();  // the previous spectrum's last stage has read X
 #pragma unroll 1
         for (int e = 0; e < E; ++e) {
@@ -315,9 +332,8 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multi(const __grid_constant__ P2
             C v[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) v[k] = park[blk * R + k];
-            const int f0 = ip_freq_of_block<G>(blk);
 #pragma unroll
-            for (int k = 0; k < R; ++k) product<KREAL>(v[k], k0, k1, f0 + k * FS);
+            for (int k = 0; k < R; ++k) sp.apply(v[k], blk * R + k);
             D2<R, +1, C>::run(v);
 #pragma unroll
             for (int k = 0; k < R; ++k) X[blk * R + k] = v[k];
@@ -348,7 +364,7 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multiclass(const __grid_constant
     pdl_begin();
     const P2v2Args& a = m.a;
     constexpr int N = G::B(0);
-    constexpr int R = G::RL, NB = N / R, FS = N / R;
+    constexpr int R = G::RL, NB = N / R;
     constexpr int E = (NB + T - 1) / T;
     extern __shared__ float4 smem_v2[];
     C* X = reinterpret_cast<C*>(smem_v2);
@@ -358,11 +374,9 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multiclass(const __grid_constant
     for (int q = 0; q < m.nclass; ++q) {
         const ColIo<C> io(m.T[q], a.ldT, a.U, a.ldU, unit);
         if (q > 0) __syncthreads();  // the previous class's last stage has read X
-        ip_first_forward<G, T, C>(X, t, a.tw, [&](int r) -> C { return r < a.H ? io.load(r) : czero<C>(); });
-        __syncthreads();
-        ip_forward<G, 1, G::S - 1, T, C>(X, t, a.tw);
-        const void *k0, *k1;
-        unit_spectra<C, KREAL>(a, q, unit, k0, k1);
+        stage_column<N, T, C>(X, io, a.H, t);
+        ip_forward<G, 0, G::S - 1, T, C>(X, t, a.tw);
+        const SpecIo<C, KREAL> sp(a.K[q], a.ldK, unit);
         // each thread accumulates only the elements it owns
 #pragma unroll 1
         for (int e = 0; e < E; ++e) {
@@ -372,10 +386,9 @@ __global__ void __launch_bounds__(T, MINB) p2v2_multiclass(const __grid_constant
 #pragma unroll
             for (int k = 0; k < R; ++k) v[k] = X[blk * R + k];
             D2<R, -1, C>::run(v);
-            const int f0 = ip_freq_of_block<G>(blk);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                product<KREAL>(v[k], k0, k1, f0 + k * FS);
+                sp.apply(v[k], blk * R + k);
                 acc[blk * R + k] = q == 0 ? v[k] : c_add(acc[blk * R + k], v[k]);
             }
         }
@@ -428,6 +441,7 @@ __global__ void __launch_bounds__(T, MINB) p3v2(const P3v2Args a)
     const int r0 = ROWS * unit;
     const float4* Us = a.U + (long long)sidx * a.specU;
     const int ncp = (int)pair_count(a.ncols);
+#pragma unroll 2
     for (int q = t; q < ncp; q += T) {
         float4 u[ROWS];
 #pragma unroll

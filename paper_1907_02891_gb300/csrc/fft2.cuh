@@ -259,28 +259,46 @@ template <int R, int DIR, class C> struct D2 {
 };
 
 // ---------------------------------------------------------------------------
-// Twiddles.  Stage s (s < S-1) has the table W[(k-1) D_s + j] =
-// exp(-i 2 pi j k / B_s), 1 <= k < R_s, j < D_s, stored as float4
-// {cos, cos, sin, sin} (the value and its pair form for two transforms).
+// Twiddles.  One table per length, W[i] = exp(-i 2 pi i / N), i < N, as
+// {cos, sin} (TwTab2::w).  Stage s needs exp(-i 2 pi j k / B_s) =
+// W[(j k N / B_s) mod N]; the exponent of k is k times that of k = 1, so it is
+// stepped by one addition and a conditional subtraction.  All stages and all
+// blocks of an SM share the one table, which stays in L1.
 // ---------------------------------------------------------------------------
-// (TwTab2, lp_internal.h: the per-stage tables and the position table)
-
 // v *= w (DIR < 0, the forward twiddle) or v *= conj(w) (DIR > 0)
 template <int DIR>
-__device__ __forceinline__ void tw_apply(CP& v, float4 w)
+__device__ __forceinline__ void tw_apply(CP& v, float2 w)
 {
-    const float2 wr = make_float2(w.x, w.y);
-    const float2 ws = make_float2(w.z, w.w);
-    const float2 wi = DIR < 0 ? ws : neg2(ws);
-    const float2 nwi = DIR < 0 ? neg2(ws) : ws;
+    const float2 wr = pk(w.x);
+    const float2 wi = pk(DIR < 0 ? w.y : -w.y);
+    const float2 nwi = pk(DIR < 0 ? -w.y : w.y);
     const CP r{fma2(v.y, nwi, mul2(v.x, wr)), fma2(v.x, wi, mul2(v.y, wr))};
     v = r;
 }
 template <int DIR>
-__device__ __forceinline__ void tw_apply(float2& v, float4 w)
+__device__ __forceinline__ void tw_apply(float2& v, float2 w)
 {
-    const float c = w.x, s = DIR < 0 ? w.z : -w.z;
+    const float c = w.x, s = DIR < 0 ? w.y : -w.y;
     v = make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// the R-1 twiddles of butterfly j of a stage with block size Bs, applied to
+// v[1..R-1]; the loads are issued first, all together
+template <int N, int R, int Bs, int DIR, class C>
+__device__ __forceinline__ void twiddle_all(C (&v)[R], int j, const float2* __restrict__ W)
+{
+    constexpr int STEP = N / Bs;
+    const int e1 = j * STEP;  // < N / R_s
+    float2 w[R - 1];
+    int e = 0;
+#pragma unroll
+    for (int k = 1; k < R; ++k) {
+        e += e1;
+        if (e >= N) e -= N;
+        w[k - 1] = __ldg(W + e);
+    }
+#pragma unroll
+    for (int k = 1; k < R; ++k) tw_apply<DIR>(v[k], w[k - 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,22 +341,6 @@ __device__ __forceinline__ int ip_base(int b, int& j)
     }
 }
 
-// frequency held by position blk * R_{S-1} + 0 after the forward stages
-template <class G>
-__device__ __forceinline__ int ip_freq_of_block(int blk)
-{
-    int f = 0, scale = 1, rem = blk;
-    (void)rem;
-    sfor<0, G::S - 1>([&](auto S_) {
-        constexpr int s = decltype(S_)::value;
-        constexpr int unit = G::D(s) / G::RL;  // blk units per digit k_s
-        const int ks = (blk / unit) % G::r(s);
-        f += ks * scale;
-        scale *= G::r(s);
-    });
-    return f;
-}
-
 // One in-place stage over the elements X[0..N) of shared memory, T threads.
 // FWD: DIF (DFT then twiddle); else DIT (conjugate twiddle then DFT).
 template <class G, int s, bool FWD, int T, class C>
@@ -353,22 +355,11 @@ __device__ __forceinline__ void ip_stage(C* X, int t, const TwTab2& tw)
         int j;
         const int base = ip_base<G, s>(b, j);
         C v[R];
-        if constexpr (!FWD && Ds > 1) {
-            const float4* w = tw.p[s] + j;
 #pragma unroll
-            for (int k = 0; k < R; ++k) v[k] = X[base + k * Ds];
-#pragma unroll
-            for (int k = 1; k < R; ++k) tw_apply<+1>(v[k], __ldg(w + (k - 1) * Ds));
-        } else {
-#pragma unroll
-            for (int k = 0; k < R; ++k) v[k] = X[base + k * Ds];
-        }
+        for (int k = 0; k < R; ++k) v[k] = X[base + k * Ds];
+        if constexpr (!FWD && Ds > 1) twiddle_all<G::B(0), R, G::B(s), +1>(v, j, tw.w);
         D2<R, FWD ? -1 : +1, C>::run(v);
-        if constexpr (FWD && Ds > 1) {
-            const float4* w = tw.p[s] + j;
-#pragma unroll
-            for (int k = 1; k < R; ++k) tw_apply<-1>(v[k], __ldg(w + (k - 1) * Ds));
-        }
+        if constexpr (FWD && Ds > 1) twiddle_all<G::B(0), R, G::B(s), -1>(v, j, tw.w);
 #pragma unroll
         for (int k = 0; k < R; ++k) X[base + k * Ds] = v[k];
     }
@@ -413,11 +404,7 @@ __device__ __forceinline__ void ip_first_forward(C* X, int t, const TwTab2& tw, 
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = ld(j + m * Ds);
         D2<R, -1, C>::run(v);
-        if constexpr (Ds > 1) {
-            const float4* w = tw.p[0] + j;
-#pragma unroll
-            for (int k = 1; k < R; ++k) tw_apply<-1>(v[k], __ldg(w + (k - 1) * Ds));
-        }
+        if constexpr (Ds > 1) twiddle_all<G::B(0), R, G::B(0), -1>(v, j, tw.w);
 #pragma unroll
         for (int k = 0; k < R; ++k) X[j + k * Ds] = v[k];
     }
@@ -438,24 +425,20 @@ __device__ __forceinline__ void ip_last_inverse(const C* X, int t, const TwTab2&
         C v[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) v[k] = X[j + k * Ds];
-        if constexpr (Ds > 1) {
-            const float4* w = tw.p[0] + j;
-#pragma unroll
-            for (int k = 1; k < R; ++k) tw_apply<+1>(v[k], __ldg(w + (k - 1) * Ds));
-        }
+        if constexpr (Ds > 1) twiddle_all<G::B(0), R, G::B(0), +1>(v, j, tw.w);
         D2<R, +1, C>::run(v);
 #pragma unroll
         for (int m = 0; m < R; ++m) st(j + m * Ds, v[m]);
     }
 }
 
-// The forward's last stage, a per-frequency operation, and the inverse's
-// first stage on the same registers: op(k, f, v) is applied to the value v
-// of frequency f (k = index within the butterfly).
+// The forward's last stage, a per-element operation, and the inverse's
+// first stage on the same registers: op(p, v) is applied to the value v at
+// position p (the frequency held there is given by the position table).
 template <class G, int T, class C, class Op>
 __device__ __forceinline__ void ip_middle(C* X, int t, Op&& op)
 {
-    constexpr int R = G::RL, NB = G::B(0) / R, FS = G::B(0) / R;  // frequency step
+    constexpr int R = G::RL, NB = G::B(0) / R;
     constexpr int E = (NB + T - 1) / T;
 #pragma unroll 1
     for (int e = 0; e < E; ++e) {
@@ -465,13 +448,33 @@ __device__ __forceinline__ void ip_middle(C* X, int t, Op&& op)
 #pragma unroll
         for (int k = 0; k < R; ++k) v[k] = X[blk * R + k];
         D2<R, -1, C>::run(v);
-        const int f0 = ip_freq_of_block<G>(blk);
 #pragma unroll
-        for (int k = 0; k < R; ++k) op(k, f0 + k * FS, v[k]);
+        for (int k = 0; k < R; ++k) op(blk * R + k, v[k]);
         D2<R, +1, C>::run(v);
 #pragma unroll
         for (int k = 0; k < R; ++k) X[blk * R + k] = v[k];
     }
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (the transform's input staged in
+// shared memory with every load in flight at once; cp.async.wait_group is a
+// hardware wait)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 }  // namespace lpk

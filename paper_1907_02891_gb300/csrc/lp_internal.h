@@ -20,12 +20,11 @@ struct P2v2Args;
 struct P3v2Args;
 struct P2Mv2Args;
 
-// Tables of the in-place engine (fft2.cuh) for one length: per stage s < S-1
-// the twiddles exp(-i 2 pi j k / B_s) at [(k-1) D_s + j] as float4
-// {cos, cos, sin, sin} (value and two-transform pair form), and the position
-// of every frequency after the forward transform.
+// Tables of the in-place engine (fft2.cuh) for one length N: the twiddles
+// W[i] = exp(-i 2 pi i / N), i < N, as {cos, sin}, and the position of every
+// frequency after the forward transform.
 struct TwTab2 {
-    const float4* p[8];
+    const float2* w;
     const unsigned short* pos;
 };
 
@@ -64,8 +63,12 @@ cudaError_t psf_fingerprint_launch(const double* K, long long n, unsigned long l
 cudaError_t psf_symmetry_launch(const double* K, int hk, int wk, int* d_asym, cudaStream_t st);
 // *d_diff |= 1 where a[i] and b[i] differ in any bit (i < n)
 cudaError_t psf_compare_launch(const double* a, const double* b, long long n, int* d_diff, cudaStream_t st);
+// pos = NULL: natural layout (rows c of ldK frequencies; the tensor-core
+// pass); else the FP32 column pass's layout (column pairs, position order)
 cudaError_t psf_spectrum_build(const double* K, int hk, int wk, int Ny, int Nx, int real_only,
                                void* dst, long long ldK, double2* W1, double2* W1b,
-                               double2* W2a, double2* W2b, cudaStream_t st);
+                               double2* W2a, double2* W2b, const unsigned short* pos, cudaStream_t st);
+cudaError_t psf_copy_natural_launch(const void* src, int ny, int ncols, long long ldK, int real_only,
+                                    const unsigned short* pos, float* dst, cudaStream_t st);
 
 }  // namespace lpk
