@@ -213,22 +213,13 @@ def ip_plan(n: int) -> dict:
     if 8 * n + 1024 > SMEM_SM:
         raise ValueError(f"length {n} does not fit shared memory")
     esize = 16 if pair else 8
-    facs = _ip_factorizations(n)
-    smin = min(len(f) for f in facs)
-    # arithmetic cost first (cheap), over the multisets with at most one
-    # stage more than the fewest; then orders and launch shapes of the best
-    def arith(f):
-        return sum(DFT_COST[r] + STAGE_COST + TW_COST for r in f)
-    cands = sorted({tuple(sorted(f)) for f in facs if len(f) <= smin + 1}, key=arith)[:6]
     best = None
-    for f in cands:
+    for f in _ip_factorizations(n):
         for perm in set(itertools.permutations(f)):
-            if perm[-1] % 2 == 0 and any(r % 2 for r in perm):
-                continue   # an even last radix conflicts in the last stage
             c = ip_cost(n, perm, esize)
             T, blocks, score = ip_launch(n, perm, pair)
             total = c / max(score, 1e-3)
-            key = (total, len(perm))
+            key = (total, len(perm), -perm[-1] % 2)
             if best is None or key < best[0]:
                 best = (key, perm, T, blocks)
     _, rs, T, blocks = best
@@ -278,12 +269,6 @@ def plan_table() -> Dict[int, dict]:
                      db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)))
             if e["tt"]:
                 e["threads"] = e["tt"]
-        # in-place engine: the measured plan ("v2" entry) where there is one
-        e.update(ip_plan(n))
-        v2 = (t or {}).get("v2")
-        if v2:
-            e.update(ip=list(v2["ip"]), pair=list(v2["pair"]), t=list(v2["t"]), m=list(v2["m"]),
-                     batch=bool(v2.get("batch", True)))
         table[n] = e
     return table
 
@@ -449,31 +434,23 @@ def _write_if_changed(path: str, text: str) -> None:
         fh.write(text)
 
 
-def _tu_text(n: int, p: dict) -> str:
-    """Translation unit of one length: p holds the tensor-core pass's
-    Stockham plan (radices, tt) and the in-place engine's plan (ip, pair, t,
-    m, batch)."""
-    r = list(p["radices"])
-    ip = list(p["ip"])
-    ctype = lambda x: "CP" if x else "float2"
-    return _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), ns=len(r), tt=p.get("tt", 0),
-                           rad6=", ".join(map(str, r + [0] * (6 - len(r)))),
-                           ipseq=", ".join(map(str, ip)), ipns=len(ip),
-                           iprad8=", ".join(map(str, ip + [0] * (8 - len(ip)))),
-                           pairs=", ".join(str(int(x)) for x in p["pair"]),
-                           t1=p["t"][0], t2=p["t"][1], t3=p["t"][2],
-                           m1=p["m"][0], m2=p["m"][1], m3=p["m"][2],
-                           c1=ctype(p["pair"][0]), c2=ctype(p["pair"][1]), c3=ctype(p["pair"][2]),
-                           batch=_b(p.get("batch", True)))
-
-
 def generate() -> List[str]:
     os.makedirs(GEN, exist_ok=True)
     table = plan_table()
     files = []
     for n, p in table.items():
+        r = list(p["radices"])
+        text = _SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=p["f1"], f3=p["f3"], ns=len(r),
+                               tt=p.get("tt", 0),
+                               upb1=p["upb"][0], upb2=p["upb"][1], upb3=p["upb"][2],
+                               minb1=p["minb"][0], minb2=p["minb"][1], minb3=p["minb"][2],
+                               kstage="true" if p["kstage"] else "false",
+                               pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
+                               db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
+                               batch=_b(p.get("batch", True)),
+                               rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
-        _write_if_changed(path, _tu_text(n, p))
+        _write_if_changed(path, text)
         files.append(path)
     decls = "\n".join(f"extern const SizeKernels kSize_{n};" for n in table)
     ptrs = ", ".join(f"&kSize_{n}" for n in table)

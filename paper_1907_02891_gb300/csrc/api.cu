@@ -18,7 +18,6 @@
 #include <vector>
 
 #include "../../include/lp.h"
-#include "conv2.cuh"
 #include "conv_kernels.cuh"
 #include "lp_internal.h"
 #include "tc_kernels.cuh"
@@ -266,33 +265,6 @@ static void fill_tc_steps(const int* r, int ns, int dir, float2* dst)
     }
 }
 
-// Twiddles of the in-place engine: W[i] = exp(-i 2 pi i / N), i < N, as
-// {cos, sin}, computed in FP64.
-static void fill_ip_twiddles(int N, float2* w)
-{
-    for (long i = 0; i < N; ++i) {
-        const double th = 2.0 * M_PI * (double)i / (double)N;
-        w[i] = make_float2((float)std::cos(th), (float)-std::sin(th));
-    }
-}
-
-// position of every frequency after the in-place forward transform:
-// position p = sum_s k_s D_s holds frequency k_0 + R_0 (k_1 + R_1 (...))
-static void fill_ip_positions(int N, const int* rs, int ns, uint16_t* pos)
-{
-    for (long p = 0; p < N; ++p) {
-        long B = N, f = 0, scale = 1;
-        for (int s = 0; s < ns; ++s) {
-            const long D = B / rs[s];
-            const long ks = (p / D) % rs[s];
-            f += ks * scale;
-            scale *= rs[s];
-            B = D;
-        }
-        pos[f] = (uint16_t)p;
-    }
-}
-
 lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
 {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
@@ -303,36 +275,31 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
     }
     const SizeKernels* k = find_size(N);
     if (!k) return lp_fail(LP_ERR_UNSUPPORTED, "FFT length %d is not built into this library", N);
-    if (N > 65535) return lp_fail(LP_ERR_UNSUPPORTED, "FFT length %d exceeds the position table", N);
-    // one device block: in-place engine twiddles (float2), positions
-    // (uint16), then the tensor-core pass's Stockham twiddles (float2) and,
-    // 256-byte aligned, its split-BF16 DFT matrices and step factors
-    const size_t pos_off = ((size_t)N * sizeof(float2) + 15) / 16 * 16;
-    const size_t chain_off = (pos_off + (size_t)N * sizeof(uint16_t) + 15) / 16 * 16;
     int fwd[6], rev[6];
-    const int ns = k->tc_nstages;
+    const int ns = k->nstages;
     for (int s = 0; s < ns; ++s) {
-        fwd[s] = k->tc_radices[s];
-        rev[s] = k->tc_radices[ns - 1 - s];
+        fwd[s] = k->radices[s];
+        rev[s] = k->radices[ns - 1 - s];
     }
     const size_t nf = chain_table_entries(fwd, ns), nr = chain_table_entries(rev, ns);
-    const size_t tw_end = chain_off + (nf + nr + 1) * sizeof(float2);
-    const size_t tc_off = (tw_end + 255) / 256 * 256;
+    // one device block: twiddle tables, then (256-byte aligned) the split
+    // DFT matrices of the tensor-core column pass where this length has one
+    const size_t tw_bytes = (nf + nr + 1) * sizeof(float2);
+    const size_t tc_off = (tw_bytes + 255) / 256 * 256;
     // (matrices of the forward stages -- the inverse chain runs in the
     // conjugate domain on the same ones --, then the step factors of the
     // forward and of the reversed chain, both with the forward sign)
     const size_t tcf = k->tc_smem > 0 ? tc_chain_bytes(fwd, ns) : 0;
     const size_t tsf = k->tc_smem > 0 ? tc_step_bytes(fwd, ns) : 0;
     const size_t tsr = k->tc_smem > 0 ? tc_step_bytes(rev, ns) : 0;
-    const size_t total = k->tc_smem > 0 ? tc_off + (tcf + tsf + tsr + 15) / 16 * 16 : tw_end;
+    const size_t total = k->tc_smem > 0 ? tc_off + (tcf + tsf + tsr + 15) / 16 * 16 : tw_bytes;
     std::vector<unsigned char> host(total, 0);
-    fill_ip_twiddles(N, reinterpret_cast<float2*>(host.data()));
-    fill_ip_positions(N, k->radices, k->nstages, reinterpret_cast<uint16_t*>(host.data() + pos_off));
+    float2* htw = reinterpret_cast<float2*>(host.data());
     std::vector<float2> tw(nf + nr + 1);
     size_t of[6] = {0}, orv[6] = {0};
     fill_chain_tables(fwd, ns, tw, 0, of);
     fill_chain_tables(rev, ns, tw, nf, orv);
-    std::memcpy(host.data() + chain_off, tw.data(), tw.size() * sizeof(float2));
+    std::memcpy(htw, tw.data(), tw.size() * sizeof(float2));
     if (k->tc_smem > 0) {
         fill_tc_mats(fwd, ns, -1, reinterpret_cast<uint16_t*>(host.data() + tc_off));
         fill_tc_steps(fwd, ns, -1, reinterpret_cast<float2*>(host.data() + tc_off + tcf));
@@ -350,15 +317,11 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
         lp_ctx_free(ctx, d, rec->bytes);
         return lp_fail(LP_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e));
     }
-    char* base = static_cast<char*>(d);
-    rec->ip.w = reinterpret_cast<const float2*>(base);
-    rec->ip.pos = reinterpret_cast<const unsigned short*>(base + pos_off);
-    float2* chain = reinterpret_cast<float2*>(base + chain_off);
     for (int s = 0; s < 6; ++s) {
-        rec->fwd.p[s] = s < ns ? chain + of[s] : nullptr;
-        rec->rev.p[s] = s < ns ? chain + orv[s] : nullptr;
+        rec->fwd.p[s] = s < ns ? rec->tw + of[s] : nullptr;
+        rec->rev.p[s] = s < ns ? rec->tw + orv[s] : nullptr;
     }
-    if (k->tc_smem > 0) rec->tc_tables = base + tc_off;
+    if (k->tc_smem > 0) rec->tc_tables = static_cast<char*>(d) + tc_off;
     *out = rec.get();
     ctx->plans.emplace(N, std::move(rec));
     return LP_OK;
@@ -507,8 +470,8 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     }
     // plans used later by lp_map (allocating here keeps lp_map allocation-free
     // once its workspace exists)
-    const PlanRec *pr, *pry;
-    lp_status s0 = lp_get_plan(ctx, Ny, &pry);
+    const PlanRec* pr;
+    lp_status s0 = lp_get_plan(ctx, Ny, &pr);
     if (s0 != LP_OK) return s0;
     s0 = lp_get_plan(ctx, Nx, &pr);
     if (s0 != LP_OK) return s0;
@@ -568,12 +531,9 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
             return LP_OK;
         }
     }
-    // FP32: the column pass's layout (column pairs in position order);
-    // split precision: natural layout, one row per column-frequency
     const int ncols = Nx / 2 + 1;
     const long long ldK = ((long long)Ny + 31) / 32 * 32;
-    const size_t bytes = split ? (size_t)ncols * ldK * (is_real ? 4 : 8)
-                               : (size_t)pair_count(ncols) * ldK * (is_real ? 8 : 16);
+    const size_t bytes = (size_t)ncols * ldK * (is_real ? 4 : 8);
     auto spec = new (std::nothrow) lp_spectrum();
     if (!spec) {
         cudaFreeAsync(d_fp, st);
@@ -625,7 +585,7 @@ extern "C" lp_status lp_kernel_spectrum(lp_ctx* ctx, const double* K, int hk, in
     if (e == cudaSuccess)
         e = psf_spectrum_build(K, hk, wk, Ny, Nx, is_real, dptr, ldK, (double2*)scratch,
                                (double2*)(scratch + w1), (double2*)(scratch + 2 * w1),
-                               (double2*)(scratch + 2 * w1 + w2), split ? nullptr : pry->ip.pos, st);
+                               (double2*)(scratch + 2 * w1 + w2), st);
     cudaFreeAsync(scratch, st);
     for (int i = 0; e == cudaSuccess && i < lp_spectrum::kUseSlots; ++i)
         e = cudaEventCreateWithFlags(&spec->use_event[i], cudaEventDisableTiming);
@@ -679,15 +639,6 @@ extern "C" lp_status lp_spectrum_copy(const lp_spectrum* s, float* dst, size_t d
         return lp_fail(LP_ERR_INVALID, "lp_spectrum_copy: destination holds %zu floats, need %zu",
                        dst_floats, ncols * s->ny * per);
     DeviceGuard dg(s->ctx->device);
-    if (s->prec == LP_PREC_FP32) {
-        // stored in the column pass's layout: gather back to natural order
-        const PlanRec* py;
-        lp_status st = lp_get_plan(s->ctx, s->ny, &py);
-        if (st != LP_OK) return st;
-        CUDA_TRY(psf_copy_natural_launch(s->data, s->ny, (int)ncols, s->ldK, s->is_real, py->ip.pos, dst,
-                                         static_cast<cudaStream_t>(stream)));
-        return LP_OK;
-    }
     CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)s->ny * per * 4, s->data, (size_t)s->ldK * per * 4,
                                (size_t)s->ny * per * 4, ncols, cudaMemcpyDeviceToDevice,
                                static_cast<cudaStream_t>(stream)));
@@ -813,15 +764,16 @@ void lp_note_spectra_used(lp_ctx* ctx, const lp_spectrum* const* spectra, int n,
 // ---------------------------------------------------------------------------
 // map
 // ---------------------------------------------------------------------------
-// workspace layout: T (ncp column pairs x ldT rows), then U (n x ncp x ldU),
-// float4 elements (column-pair layout of conv2.cuh), then the parked
-// forward column spectra of a batched column pass
+static inline long long even_up(long long x) { return (x + 1) / 2 * 2; }
+
+// workspace layout: T (ncolsT x ldT) then U (n x ncolsU x ldU), complex64,
+// both column-blocked
 static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mode, MapDims* d)
 {
     d->ncols = nx / 2 + 1;
-    d->ncp = pair_count(d->ncols);
-    d->ldT = pair_ld(h);
-    d->ny = ny;
+    d->ncolsT = t_cols_alloc(d->ncols);
+    d->ncolsU = u_cols_alloc(d->ncols);
+    d->ldT = even_up(h);
     if (mode == LP_OUT_FULL) {
         d->Hout = h + hk - 1;
         d->Wout = w + wk - 1;
@@ -835,20 +787,14 @@ static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mo
         d->r0 = 0;
         d->c0 = 0;
     }
-    d->ldU = pair_ld(d->Hout);
+    d->ldU = even_up(d->Hout);
     d->prec = (int)LP_PREC_FP32;
-    const SizeKernels* k = find_size(ny);
-    d->batch = (k && k->batch) ? 1 : 0;
 }
-
-size_t lp_park_bytes(const MapDims& d) { return 16ull * (size_t)d.ncp * (size_t)d.ny; }
 
 size_t lp_workspace_bytes(const MapDims& d, int n)
 {
     const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    const bool park = nchunk > 1 && d.batch && d.prec == (int)LP_PREC_FP32;
-    return 16ull * ((size_t)d.ncp * (size_t)d.ldT + (size_t)d.ncp * (size_t)nchunk * (size_t)d.ldU) +
-           (park ? lp_park_bytes(d) : 0) + 256;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
 }
 
 extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
@@ -897,58 +843,53 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     return LP_OK;
 }
 
-// Map rows per work unit of the row passes: four (two transforms per
-// block) or two.
-static inline int unit_rows(const PlanRec* px, int pass) { return px->k->pair[pass] ? 4 : 2; }
-
-// The three passes as separate launches (row units [u0, u1) for the row
-// passes), composed by lp_launch_map and by the banded host-buffer map.
+// The three passes as separate launches (row pairs [pair0, pair1) for the
+// row passes), composed by lp_launch_map and by the banded host-buffer map.
 static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float* L, int h, int w, int ldl,
-                                     const MapDims& d, float4* T, int u0, int u1, cudaStream_t st)
+                                     const MapDims& d, float2* T, int pair0, int pair1, cudaStream_t st)
 {
-    P1v2Args a1;
+    P1Args a1;
     a1.L = L;
     a1.ldl = ldl;
     a1.H = h;
     a1.W = w;
+    a1.Wst = (w + 3) / 4 * 4;
+    a1.vec16 = ((reinterpret_cast<uintptr_t>(L) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
     a1.T = T;
     a1.ldT = d.ldT;
-    a1.unit0 = u0;
-    a1.units = u1;
+    a1.pair0 = pair0;
+    a1.npairs = pair1;
     a1.ncols = d.ncols;
-    a1.tw = px->ip;
-    if (u1 <= u0) return LP_OK;
+    a1.tw = px->fwd;
     const int tok = lp_pass_begin(ctx, 0, st);
     CUDA_TRY(px->k->p1(a1, st));
     lp_pass_end(ctx, tok, st);
     return LP_OK;
 }
 
-// column pass for spectra [base, base+cnt) into U (cnt blocks of ncp x ldU)
+// column pass for spectra [base, base+cnt) into U (cnt blocks of ncols x ldU)
 static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectrum* const* spectra, int base,
-                                int cnt, int h, const MapDims& d, const float4* T, float4* U, float4* park,
-                                cudaStream_t st)
+                                int cnt, int h, const MapDims& d, const float2* T, float2* U, cudaStream_t st)
 {
     const lp_spectrum* s0 = spectra[0];
-    const long long specU = d.ncp * d.ldU;
     if (d.prec == (int)LP_PREC_SPLIT_BF16) {
         // tensor-core column pass: one launch per spectrum
         for (int i = 0; i < cnt; ++i) {
             P2TcArgs a2;
             P2Args& b = a2.a;
-            b.T = reinterpret_cast<const float2*>(T);
+            b.T = T;
             b.ldT = d.ldT;
             b.H = h;
             for (int q = 0; q < kMaxSpectraPerLaunch; ++q) b.K[q] = nullptr;
             b.K[0] = spectra[base + i]->data;
             b.ldK = s0->ldK;
             b.nspec = 1;
-            b.U = reinterpret_cast<float2*>(U + (size_t)i * specU);
+            b.U = U + (size_t)i * d.ncolsU * d.ldU;
             b.ldU = d.ldU;
-            b.specU = specU;
+            b.specU = (long long)d.ncolsU * d.ldU;
             b.r0 = d.r0;
             b.Hout = d.Hout;
-            b.HoutPad = d.Hout;
+            b.HoutPad = (int)d.ldU;
             b.ncols = d.ncols;
             b.twf = py->fwd;
             b.twi = py->rev;
@@ -968,7 +909,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
         const int kind = spectra[base + k0]->is_real;
         int k1 = k0;
         while (k1 < cnt && spectra[base + k1]->is_real == kind) ++k1;
-        P2v2Args a2;
+        P2Args a2;
         a2.T = T;
         a2.ldT = d.ldT;
         a2.H = h;
@@ -976,14 +917,15 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             a2.K[i] = (i < k1 - k0) ? spectra[base + k0 + i]->data : nullptr;
         a2.ldK = s0->ldK;
         a2.nspec = k1 - k0;
-        a2.U = U + (size_t)k0 * specU;
+        a2.U = U + (size_t)k0 * d.ncolsU * d.ldU;
         a2.ldU = d.ldU;
-        a2.specU = specU;
+        a2.specU = (long long)d.ncolsU * d.ldU;
         a2.r0 = d.r0;
         a2.Hout = d.Hout;
+        a2.HoutPad = (int)d.ldU;
         a2.ncols = d.ncols;
-        a2.park = park;
-        a2.tw = py->ip;
+        a2.twf = py->fwd;
+        a2.twi = py->rev;
         const int tok = lp_pass_begin(ctx, 1, st);
         CUDA_TRY(py->k->p2(a2, kind != 0, st));
         lp_pass_end(ctx, tok, st);
@@ -992,35 +934,26 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
     return LP_OK;
 }
 
-static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDims& d, const float4* U, int cnt,
-                                     float* const* out, int ldo, int u0, int u1, cudaStream_t st)
+static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDims& d, const float2* U, int cnt,
+                                     float* const* out, int ldo, int pair0, int pair1, cudaStream_t st)
 {
-    P3v2Args a3;
+    P3Args a3;
     a3.U = U;
     a3.ldU = d.ldU;
-    a3.specU = d.ncp * d.ldU;
+    a3.specU = (long long)d.ncolsU * d.ldU;
     a3.Hout = d.Hout;
-    a3.unit0 = u0;
-    a3.units = u1;
+    a3.pair0 = pair0;
+    a3.npairs = pair1;
     for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i < cnt ? out[i] : nullptr;
     a3.ldo = ldo;
     a3.c0 = d.c0;
     a3.Wout = d.Wout;
     a3.ncols = d.ncols;
-    a3.tw = px->ip;
-    if (u1 <= u0) return LP_OK;
+    a3.tw = px->rev;
     const int tok = lp_pass_begin(ctx, 2, st);
     CUDA_TRY(px->k->p3(a3, cnt, st));
     lp_pass_end(ctx, tok, st);
     return LP_OK;
-}
-
-// workspace pieces: T, U (spectra of one launch), park
-static inline void ws_split(const MapDims& d, void* ws, float4** T, float4** U, float4** park, int nchunk)
-{
-    *T = static_cast<float4*>(ws);
-    *U = *T + (size_t)d.ncp * d.ldT;
-    *park = *U + (size_t)d.ncp * d.ldU * (size_t)nchunk;
 }
 
 // Launch P1, P2, P3 for n spectra (the validated sequence of lp_map).
@@ -1034,18 +967,14 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     if (ps != LP_OK) return ps;
     ps = lp_get_plan(ctx, s0->nx, &px);
     if (ps != LP_OK) return ps;
-    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    float4 *T, *U, *park;
-    ws_split(d, ws, &T, &U, &park, nchunk);
-    if (!(nchunk > 1 && d.batch && d.prec == (int)LP_PREC_FP32)) park = nullptr;
+    float2* T = static_cast<float2*>(ws);
+    float2* U = T + (size_t)d.ncolsT * d.ldT;
     if ((ps = lp_wait_spectra_built(spectra, n, st)) != LP_OK) return ps;
-    const int r1 = unit_rows(px, 0), r3 = unit_rows(px, 2);
-    if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (h + r1 - 1) / r1, st)) != LP_OK) return ps;
+    if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
-        if ((ps = launch_columns(ctx, py, spectra, base, cnt, h, d, T, U, park, st)) != LP_OK) return ps;
-        if ((ps = launch_rows_inverse(ctx, px, d, U, cnt, out + base, ldo, 0, (d.Hout + r3 - 1) / r3, st)) !=
-            LP_OK)
+        if ((ps = launch_columns(ctx, py, spectra, base, cnt, h, d, T, U, st)) != LP_OK) return ps;
+        if ((ps = launch_rows_inverse(ctx, px, d, U, cnt, out + base, ldo, 0, (int)(d.ldU / 2), st)) != LP_OK)
             return ps;
     }
     // recorded after the last pass (an event between the passes would stop
@@ -1167,10 +1096,8 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     void* ws = nullptr;
     st = lp_get_workspace(ctx, c, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
-    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    float4 *T, *U, *park;
-    ws_split(d, ws, &T, &U, &park, nchunk);
-    if (!(nchunk > 1 && d.batch && d.prec == (int)LP_PREC_FP32)) park = nullptr;
+    float2* T = static_cast<float2*>(ws);
+    float2* U = T + (size_t)d.ncolsT * d.ldT;
     cudaEvent_t* ev = ctx->hs_events.data();
     cudaEvent_t ev_start = ev[0], ev_end = ev[1];
     cudaEvent_t* ev_in = ev + 2;                 // kHostBands
@@ -1192,12 +1119,11 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_start, 0));
     for (int k = 0; k < n; ++k) CUDA_TRY(cudaStreamWaitEvent(c, spectra[k]->ready, 0));
 
-    const int ru1 = unit_rows(px, 0), ru3 = unit_rows(px, 2);
-    const int nunits = (h + ru1 - 1) / ru1;
-    const int nb_in = host_bands(lbytes, nunits);
+    const int npairs = (int)(d.ldT / 2);
+    const int nb_in = host_bands(lbytes, npairs);
     for (int b = 0; b < nb_in; ++b) {
-        const int q0 = (int)((long long)nunits * b / nb_in), q1 = (int)((long long)nunits * (b + 1) / nb_in);
-        const int r0 = ru1 * q0, r1 = (ru1 * q1 < h) ? ru1 * q1 : h;
+        const int q0 = (int)((long long)npairs * b / nb_in), q1 = (int)((long long)npairs * (b + 1) / nb_in);
+        const int r0 = 2 * q0, r1 = (2 * q1 < h) ? 2 * q1 : h;
         if (r1 > r0)
             CUDA_TRY(cudaMemcpy2DAsync(dL + (size_t)r0 * w, 4ull * w, L_host + (size_t)r0 * ldl, 4ull * ldl,
                                        4ull * w, r1 - r0, cudaMemcpyHostToDevice, ctx->hs_in));
@@ -1207,19 +1133,19 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     }
     CUDA_TRY(cudaEventRecord(ev_lfree, c));  // the staging map may be overwritten after this
     ctx->hs_lfree_valid = true;
-    const int ounits = (d.Hout + ru3 - 1) / ru3;
-    const int nb_out = host_bands(obytes * (size_t)n, ounits);
+    const int opairs = (int)(d.ldU / 2);
+    const int nb_out = host_bands(obytes * (size_t)n, opairs);
     for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {
         const int cnt = (n - cb) < kMaxSpectraPerLaunch ? (n - cb) : kMaxSpectraPerLaunch;
-        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, park, c)) != LP_OK) return st;
+        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, c)) != LP_OK) return st;
         if (cb == 0 && ctx->hs_ofree_valid[obuf]) CUDA_TRY(cudaStreamWaitEvent(c, ctx->hs_ofree[obuf], 0));
         for (int b = 0; b < nb_out; ++b) {
-            const int q0 = (int)((long long)ounits * b / nb_out), q1 = (int)((long long)ounits * (b + 1) / nb_out);
+            const int q0 = (int)((long long)opairs * b / nb_out), q1 = (int)((long long)opairs * (b + 1) / nb_out);
             if ((st = launch_rows_inverse(ctx, px, d, U, cnt, dout.data() + cb, d.Wout, q0, q1, c)) != LP_OK)
                 return st;
             CUDA_TRY(cudaEventRecord(ev_out[b], c));
             CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_out[b], 0));
-            const int r0 = ru3 * q0, r1 = (ru3 * q1 < d.Hout) ? ru3 * q1 : d.Hout;
+            const int r0 = 2 * q0, r1 = (2 * q1 < d.Hout) ? 2 * q1 : d.Hout;
             if (r1 <= r0) continue;
             for (int k = cb; k < cb + cnt; ++k)
                 CUDA_TRY(cudaMemcpy2DAsync(out_host[k] + (size_t)r0 * ldo, 4ull * ldo, dout[k] + (size_t)r0 * d.Wout,
@@ -1299,16 +1225,30 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     const PlanRec *py, *px;
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
     if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
-    // workspace: the classes' T, then U, then the per-column-pair sums of
-    // the spectrum products
-    const size_t tbytes = 16ull * (size_t)d.ncp * d.ldT;
-    const size_t ubytes = 16ull * (size_t)d.ncp * d.ldU;
+    const size_t tbytes = 8ull * (size_t)d.ncolsT * d.ldT;
+    const size_t ubytes = 8ull * (size_t)d.ncolsU * d.ldU;
     void* ws = nullptr;
-    if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + lp_park_bytes(d) + 256, &ws)) != LP_OK)
-        return st;
-    float4* Tb = static_cast<float4*>(ws);
-    float4* U = Tb + (size_t)T * d.ncp * d.ldT;
-    float4* acc = U + (size_t)d.ncp * d.ldU;
+    if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + 256, &ws)) != LP_OK) return st;
+    float2* Tb = static_cast<float2*>(ws);
+    float2* U = Tb + (size_t)T * d.ncolsT * d.ldT;
+    const int npairs = (int)(d.ldT / 2);
+    if ((st = lp_wait_spectra_built(spectra, T, s)) != LP_OK) return st;
+    for (int t = 0; t < T; ++t) {
+        P1Args a1;
+        a1.L = L[t];
+        a1.ldl = ldl;
+        a1.H = h;
+        a1.W = w;
+        a1.Wst = (w + 3) / 4 * 4;
+        a1.vec16 = ((reinterpret_cast<uintptr_t>(L[t]) & 15) == 0 && ldl % 4 == 0 && w % 4 == 0) ? 1 : 0;
+        a1.T = Tb + (size_t)t * d.ncolsT * d.ldT;
+        a1.ldT = d.ldT;
+        a1.pair0 = 0;
+        a1.npairs = npairs;
+        a1.ncols = d.ncols;
+        a1.tw = px->fwd;
+        CUDA_TRY(px->k->p1(a1, s));
+    }
     // the real-spectrum kernel needs every class's spectrum real
     bool all_real = true;
     for (int t = 0; t < T; ++t) all_real = all_real && spectra[t]->is_real;
@@ -1317,39 +1257,45 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
             if (spectra[t]->is_real)
                 return lp_fail(LP_ERR_UNSUPPORTED,
                                "lp_map_multiclass: mixing real and complex spectra is not supported");
-    if ((st = lp_wait_spectra_built(spectra, T, s)) != LP_OK) return st;
-    const int r1 = unit_rows(px, 0), r3 = unit_rows(px, 2);
-    for (int t = 0; t < T; ++t)
-        if ((st = launch_rows_forward(ctx, px, L[t], h, w, ldl, d, Tb + (size_t)t * d.ncp * d.ldT, 0,
-                                      (h + r1 - 1) / r1, s)) != LP_OK)
-            return st;
-    P2Mv2Args m;
-    P2v2Args& a2 = m.a;
+    P2MArgs a2;
     for (int i = 0; i < kMaxSpectraPerLaunch; ++i) {
-        m.T[i] = i < T ? Tb + (size_t)i * d.ncp * d.ldT : nullptr;
+        a2.T[i] = i < T ? Tb + (size_t)i * d.ncolsT * d.ldT : nullptr;
         a2.K[i] = i < T ? spectra[i]->data : nullptr;
     }
-    m.nclass = T;
-    a2.T = Tb;
     a2.ldT = d.ldT;
     a2.H = h;
     a2.ldK = s0->ldK;
-    a2.nspec = T;
+    a2.nclass = T;
     a2.U = U;
     a2.ldU = d.ldU;
-    a2.specU = d.ncp * d.ldU;
     a2.r0 = d.r0;
     a2.Hout = d.Hout;
+    a2.HoutPad = (int)d.ldU;
     a2.ncols = d.ncols;
-    a2.park = acc;
-    a2.tw = py->ip;
+    a2.twf = py->fwd;
+    a2.twi = py->rev;
     {
-        const int tok = lp_pass_begin(ctx, 1, s);
-        CUDA_TRY(py->k->p2m(m, all_real, s));
-        lp_pass_end(ctx, tok, s);
+        const cudaError_t e = py->k->p2m(a2, all_real, s);
+        if (e == cudaErrorNotSupported)
+            return lp_fail(LP_ERR_UNSUPPORTED,
+                           "lp_map_multiclass: padded length %d leaves no shared memory for the "
+                           "class accumulator (supported up to about 14000)", s0->ny);
+        if (e != cudaSuccess) return lp_fail(LP_ERR_CUDA, "lp_map_multiclass: %s", cudaGetErrorString(e));
     }
-    float* outs[1] = {out};
-    if ((st = launch_rows_inverse(ctx, px, d, U, 1, outs, ldo, 0, (d.Hout + r3 - 1) / r3, s)) != LP_OK) return st;
+    P3Args a3;
+    a3.U = U;
+    a3.ldU = d.ldU;
+    a3.specU = 0;
+    a3.Hout = d.Hout;
+    a3.pair0 = 0;
+    a3.npairs = (int)(d.ldU / 2);
+    for (int i = 0; i < kMaxSpectraPerLaunch; ++i) a3.out[i] = i == 0 ? out : nullptr;
+    a3.ldo = ldo;
+    a3.c0 = d.c0;
+    a3.Wout = d.Wout;
+    a3.ncols = d.ncols;
+    a3.tw = px->rev;
+    CUDA_TRY(px->k->p3(a3, 1, s));
     lp_note_spectra_used(ctx, spectra, T, s);
     return LP_OK;
 }

@@ -29,12 +29,8 @@ struct SpecKey {
 
 struct PlanRec {
     const lpk::SizeKernels* k = nullptr;
-    float2* tw = nullptr;  // one device block: the tables below
+    float2* tw = nullptr;  // device twiddle tables (forward chain, then reversed chain)
     size_t bytes = 0;
-    // in-place engine: per-stage twiddles and the frequency -> position table
-    lpk::TwTab2 ip{};
-    // tensor-core column pass: Stockham twiddle tables (forward chain, then
-    // reversed chain)
     lpk::TwChain fwd{}, rev{};
     // tables of the tensor-core column pass (split-BF16 DFT matrices, then
     // twiddle step factors; same block as tw; null where the length has no
@@ -50,13 +46,12 @@ struct Workspace {
 
 struct MapDims {
     int ncols;          // Nx/2 + 1
-    long long ncp;      // column pairs of T and U (ncols rounded up to even, halved)
-    long long ldT, ldU; // rows stored per column pair in T and U (multiples of 4)
-    int ny;             // padded column length
+    long long ncolsT;   // columns allocated for T (ncols rounded up to its column blocks)
+    long long ncolsU;   // columns allocated per spectrum for U (likewise)
+    long long ldT, ldU; // leading dimensions of T and U (complex elements, even)
     int Hout, Wout;     // output size
     int r0, c0;         // first kept row / column of the circular result
     int prec;           // lp_precision of the column pass
-    int batch;          // several FP32 spectra share one forward column transform
 };
 
 struct ServeState;
@@ -131,11 +126,8 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                           const lp_spectrum* const* spectra, int n, const void* out, int ldo,
                           lp_outmode mode, lp_precision prec, MapDims* d);
 // bytes of one map's workspace: T, then U for up to kMaxSpectraPerLaunch
-// spectra (the spectra of one launch), then the parked forward column
-// spectra of a batched column pass (several FP32 spectra), + alignment slack
+// spectra (the spectra of one launch), + alignment slack
 size_t lp_workspace_bytes(const MapDims& d, int n);
-// parked forward column spectra: N elements per column pair, 16 bytes each
-size_t lp_park_bytes(const MapDims& d);
 lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                         const MapDims& d, void* ws, cudaStream_t st);

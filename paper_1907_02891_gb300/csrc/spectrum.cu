@@ -174,53 +174,6 @@ __global__ void psf_store_spectrum(const double2* __restrict__ W2, int Ny, int n
     }
 }
 
-// The same spectrum in the layout of the FP32 column pass: per column pair
-// q, ldK entries in the position order of the column transform (entry pos[u]
-// holds frequency u), each {K[2q][u], K[2q+1][u]} (real) or
-// {re K[2q], re K[2q+1], im K[2q], im K[2q+1]} (complex).
-__global__ void psf_store_spectrum_pairs(const double2* __restrict__ W2, int Ny, int ncols, double scale,
-                                         int real_only, float* dst, long long ldK,
-                                         const unsigned short* __restrict__ pos)
-{
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // u * ncols + c
-    if (i >= (long long)Ny * ncols) return;
-    const int u = (int)(i / ncols), c = (int)(i % ncols);
-    const double2 z = W2[i];
-    const long long e = (long long)(c >> 1) * ldK + pos[u];
-    if (real_only) {
-        dst[2 * e + (c & 1)] = (float)(z.x * scale);
-    } else {
-        dst[4 * e + (c & 1)] = (float)(z.x * scale);
-        dst[4 * e + 2 + (c & 1)] = (float)(z.y * scale);
-    }
-}
-
-// Natural layout ((nx/2+1) rows of ny, row c = column-frequency c) from the
-// column-pass layout, for inspection.
-__global__ void psf_copy_natural(const float* __restrict__ src, int ny, int ncols, long long ldK, int real_only,
-                                 const unsigned short* __restrict__ pos, float* dst)
-{
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // c * ny + u
-    if (i >= (long long)ny * ncols) return;
-    const int c = (int)(i / ny), u = (int)(i % ny);
-    const long long e = (long long)(c >> 1) * ldK + pos[u];
-    if (real_only) {
-        dst[i] = src[2 * e + (c & 1)];
-    } else {
-        dst[2 * i] = src[4 * e + (c & 1)];
-        dst[2 * i + 1] = src[4 * e + 2 + (c & 1)];
-    }
-}
-
-cudaError_t psf_copy_natural_launch(const void* src, int ny, int ncols, long long ldK, int real_only,
-                                    const unsigned short* pos, float* dst, cudaStream_t st)
-{
-    const long long n = (long long)ny * ncols;
-    psf_copy_natural<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(static_cast<const float*>(src), ny, ncols, ldK,
-                                                                  real_only, pos, dst);
-    return cudaGetLastError();
-}
-
 // order-independent 64-bit fingerprint of the PSF values (cache key).  mix64
 // is the SplitMix64 output finaliser (Steele, Lea and Flood, "Fast
 // splittable pseudorandom number generators", OOPSLA 2014): its published
@@ -273,7 +226,7 @@ cudaError_t psf_symmetry_launch(const double* K, int hk, int wk, int* d_asym, cu
 // Full spectrum build.  W1 holds hk*Nx, W2a/W2b each Ny*ncols complex128.
 cudaError_t psf_spectrum_build(const double* K, int hk, int wk, int Ny, int Nx, int real_only,
                                void* dst, long long ldK, double2* W1, double2* W1b,
-                               double2* W2a, double2* W2b, const unsigned short* pos, cudaStream_t st)
+                               double2* W2a, double2* W2b, cudaStream_t st)
 {
     const int ncols = Nx / 2 + 1;
     const int cy = (hk - 1) / 2, cx = (wk - 1) / 2;
@@ -295,12 +248,6 @@ cudaError_t psf_spectrum_build(const double* K, int hk, int wk, int Ny, int Nx, 
     double2* cols = nullptr;
     if ((e = fft64_forward(W2a, W2b, Ny, ncols, 1, ncols, 1, st, &cols)) != cudaSuccess) return e;
     const double scale = 1.0 / (2.0 * (double)Ny * (double)Nx);
-    if (pos) {
-        const long long n = (long long)Ny * ncols;
-        psf_store_spectrum_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cols, Ny, ncols, scale, real_only,
-                                                                               static_cast<float*>(dst), ldK, pos);
-        return cudaGetLastError();
-    }
     dim3 grid((ncols + 31) / 32, (Ny + 31) / 32), block(32, 8);
     psf_store_spectrum<<<grid, block, 0, st>>>(cols, Ny, ncols, scale, real_only, dst, ldK);
     return cudaGetLastError();

@@ -441,12 +441,10 @@ struct TcProductSink {
     }
 };
 
-// Inverse: output row t + k N/R0 of the circular result, kept rows to U
-// (the column's lane of the column-pair layout: re at 4 r, im at 4 r + 2
-// floats from its first element).
+// Inverse: output row t + k N/R0 of the circular result, kept rows to U.
 template <int N, int R0>
 struct TcStoreSink {
-    float* Uc;
+    float2* Uc;
     int r0, Hout, t;
     __device__ __forceinline__ void prefetch() {}
     __device__ __forceinline__ void pad() {}
@@ -454,10 +452,7 @@ struct TcStoreSink {
     {
         int rr = t + k * (N / R0) - r0;
         if (rr < 0) rr += N;
-        if (rr < Hout) {  // back from the conjugate domain
-            Uc[4 * (long long)rr] = z.x;
-            Uc[4 * (long long)rr + 2] = -z.y;
-        }
+        if (rr < Hout) Uc[u_row(rr)] = make_float2(z.x, -z.y);  // back from the conjugate domain
     }
 };
 
@@ -483,14 +478,13 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
     __syncthreads();  // the previous column's last writes of As are consumed
     // first forward stage: rows j + m N/R0 of column c (rows >= H are the zero padding)
     if (t < NB0) {
-        // column c of the column-pair layout (T as float4 elements)
-        const float* col = reinterpret_cast<const float*>(a.T) + (long long)(c >> 1) * a.ldT * 4 + (c & 1);
+        const float2* col = t_column(a.T, a.ldT, c);
         tc_zero_pad<G0>(t);
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int row = t + m * NB0;
-            tc_put<G0>(t, m, row < a.H ? make_float2(__ldg(col + 4 * (long long)row), __ldg(col + 4 * (long long)row + 2))
-                                       : make_float2(0.f, 0.f));
+            const long long off = (NB0 % 2 == 0) ? t_row(t) + m * t_row_step<NB0>() : t_row(row);
+            tc_put<G0>(t, m, row < a.H ? __ldg(col + off) : make_float2(0.f, 0.f));
         }
     }
     {
@@ -498,9 +492,10 @@ __device__ __noinline__ void tc_column(const P2TcArgs& A, int c, TcState& st)
         TcProductSink<N, RL, KREAL, GI0> ps{kcol, t};
         Fwd::run(st, a.twf, A.err, t, ps);
     }
-    float* Uc = reinterpret_cast<float*>(a.U) + (long long)(c >> 1) * a.ldU * 4 + (c & 1);
+    float2* Uc = u_column(a.U, a.ldU, c);
     TcStoreSink<N, R0> ss{Uc, a.r0, a.Hout, t};
     Inv::run(st, a.twi, A.err, t, ss);
+    if (a.HoutPad != a.Hout && t == 0) Uc[u_row(a.Hout)] = make_float2(0.f, 0.f);
 }
 
 // The column pass: persistent blocks, one column of one spectrum at a time.

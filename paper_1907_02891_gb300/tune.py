@@ -1,22 +1,21 @@
-"""Autotuner of the FFT plans per length.
+"""Autotuner of the FFT plans (radix order and launch shape) per length.
 
 For each length N it builds small variant libraries that contain only N,
-each with one candidate plan of the in-place engine (radix order, two
-transforms per block or one, threads per block, minimum resident blocks
-per SM), times the three passes of a map whose padded size is N x N on the
-GPU, and keeps, for the radix order with the best total, the best launch
-setting of each pass; with several spectra per map it also compares the
-batched column pass (one forward transform, parked) with one
-single-spectrum pass per spectrum.  The result is written to
-``tuned_plans.json`` beside this file (key "v2" of each length);
-``build.py`` uses it for every length it lists.
+each with one candidate radix sequence and one setting of the launch knobs
+of the prefetching kernels (work units per block, minimum resident blocks per
+SM, spectrum-column staging), times the three passes of a map whose padded
+size is N x N on the GPU, and keeps, for the fastest radix sequence, the best
+knob setting of each pass, then refines it (double-buffered exchange; with
+several spectra per map, one single-spectrum column pass per spectrum
+against the batched kernel).  The result is written to ``tuned_plans.json``
+beside this file; ``build.py`` uses it for every length it lists.
 
     python -m paper_1907_02891_gb300.tune --sizes 4704 [--quick] \
-        [--map-side 4096 --psf 541 --nspec 1] [--plan 12,8,7,7 ...]
+        [--map-side 4096 --psf 541 --nspec 1] [--plan 21,16,14 ...]
 
 The passes are timed one by one, with events between them, which stops the
 launch overlap between passes of a real map; check a stored plan on the
-whole map as well.
+whole map as well (a setting that speeds one pass up can slow the map down).
 
 Needs nvcc and one GPU.  Each variant is timed in a fresh subprocess (the
 variant libraries export the same symbols).
@@ -49,49 +48,23 @@ def _prod(p) -> int:
     return r
 
 
-def candidate_plans(n: int, pair: bool, limit: int = 3) -> List[Tuple[int, ...]]:
-    """Radix orders of the in-place engine with the least modelled cost."""
-    esize = 16 if pair else 8
-    facs = B._ip_factorizations(n)
-    smin = min(len(f) for f in facs)
+def candidate_plans(n: int, limit: int = 3) -> List[Tuple[int, ...]]:
+    """Radix sequences ordered like build.choose_plan, then the other orders
+    of the same multisets (first radix odd / large first)."""
     scored = []
-    for f in {tuple(sorted(f)) for f in facs if len(f) <= smin + 1}:
-        for perm in set(itertools.permutations(f)):
-            if perm[-1] % 2 == 0 and any(r % 2 for r in perm):
-                continue
-            if pair and max(perm) > 16:
-                continue
-            T, blocks, score = B.ip_launch(n, perm, pair)
-            scored.append((B.ip_cost(n, perm, esize) / max(score, 1e-3), perm))
-    scored.sort()
-    return [p for _, p in scored[:limit]]
-
-
-def launch_options(n: int, rs, pair: bool) -> List[Tuple[int, int]]:
-    """(threads per block, minimum resident blocks) around the planner's
-    choice: its own, and the best-balanced shapes with one resident block
-    more or less."""
-    esize = 16 if pair else 8
-    regs = B.ip_regs(rs, pair)
-    by_smem = B.SMEM_SM // (n * esize + 1024)
-    out = []
-    T0, m0, _ = B.ip_launch(n, rs, pair)
-    out.append((T0, m0))
-    for m in sorted({m0 - 1, m0 + 1, by_smem}):
-        if m < 1 or m > by_smem:
+    for f in B.factorizations(n):
+        if B.threads_for(n, f) > B.MAX_THREADS:
             continue
-        best = None
-        for T in range(64, 1025, 32):
-            if T * m > 2048 or 65536 // (T * m) < min(regs, 96) - 8:
-                continue
-            nbs = [n // r for r in rs]
-            eff = sum(nbs) / (T * sum((x + T - 1) // T for x in nbs))
-            key = eff * min(1.0, T * m / 32 / 20.0)
-            if best is None or key > best[0] + 1e-9:
-                best = (key, T)
-        if best and (best[1], m) not in out:
-            out.append((best[1], m))
-    return out
+        scored.append(((len(f), max(f), -min(f)), f))
+    scored.sort()
+    out: List[Tuple[int, ...]] = []
+    for _, f in scored:
+        for perm in (tuple(sorted(f, reverse=True)), tuple(sorted(f))):
+            if perm not in out:
+                out.append(perm)
+        if len(out) >= limit:
+            break
+    return out[:limit]
 
 
 def _compile_common(jobs: int) -> List[str]:
@@ -112,7 +85,16 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
     if os.path.exists(lib):
         return lib
     os.makedirs(d, exist_ok=True)
-    text = B._tu_text(n, plan)
+    r = list(plan["radices"])
+    text = B._SIZE_TU.format(n=n, seq=", ".join(map(str, r)), f1=plan["f1"], f3=plan["f3"], ns=len(r),
+                             tt=plan.get("tt", 0),
+                             upb1=plan["upb"][0], upb2=plan["upb"][1], upb3=plan["upb"][2],
+                             minb1=plan["minb"][0], minb2=plan["minb"][1], minb3=plan["minb"][2],
+                             kstage="true" if plan["kstage"] else "false",
+                             pf1=B._b(plan["pf"][0]), pf2=B._b(plan["pf"][1]), pf3=B._b(plan["pf"][2]),
+                             db1=B._b(plan["db"][0]), db2=B._b(plan["db"][1]), db3=B._b(plan["db"][2]),
+                             batch=B._b(plan.get("batch", True)),
+                             rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
     src = os.path.join(d, f"size_{n}.cu")
     with open(src, "w") as fh:
         fh.write(text)
@@ -180,15 +162,33 @@ def time_variant(lib: str, n: int, reps: int, side: int = 0, psf: int = 0, nspec
 
 def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int = 0, psf: int = 0,
               nspec: int = 1, plans: List[Tuple[int, ...]] = ()) -> dict:
-    base = B.plan_table()[n]
-    pairs = [1, 0] if 16 * n + 1024 <= B.SMEM_SM else [0]
+    base = B.plan_table_entry(n)
+    plans = list(plans) or candidate_plans(n, 2 if quick else 3)
+    knobs = []
+    for upb, minb, kst in itertools.product((1, 2, 3), (1, 2, 3), (False, True)):
+        if quick and (minb == 3 and upb == 1):
+            continue
+        if upb == 3 and (quick or kst):
+            continue
+        knobs.append((upb, minb, kst, 1))
+    knobs.append((1, 1, False, 0))   # one-unit-per-block kernels (no prefetch)
+    knobs.append((1, 2, False, 0))
+    knobs.append((1, 3, False, 0))
     variants = []
-    for pair in pairs:
-        rlist = [tuple(p) for p in plans] or candidate_plans(n, bool(pair), 2 if quick else 3)
-        for rs in rlist:
-            for T, m in launch_options(n, rs, bool(pair)):
+    for r in plans:
+        # threads per transform: one butterfly per thread in every stage (0),
+        # or as many as the stage with the fewest butterflies (whole warps)
+        tts = [0]
+        few = (n // max(r) + 31) // 32 * 32
+        if few < B.threads_for(n, r):
+            tts.append(few)
+        for tt in tts:
+            for upb, minb, kst, pf in knobs:
+                if tt and (kst or not pf):   # staging / no-prefetch only at the default thread count
+                    continue
                 p = dict(base)
-                p.update(ip=list(rs), pair=[pair] * 3, t=[T] * 3, m=[m] * 3, batch=True)
+                p.update(radices=list(r), threads=tt or B.threads_for(n, r), upb=[upb] * 3,
+                         minb=[minb] * 3, kstage=kst, tt=tt, pf=[pf] * 3, db=[0, 0, 0])
                 variants.append(p)
     t0 = time.time()
 
@@ -201,54 +201,96 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
     with cf.ThreadPoolExecutor(jobs) as ex:
         libs = list(ex.map(build_or_error, variants))
     log(f"N={n}: built {sum(isinstance(l, str) for l in libs)} of {len(libs)} variants in {time.time() - t0:.0f} s")
-    reps = 200 if n <= 5200 else 40
     results = []
     for p, lib in zip(variants, libs):
-        tag = f"{p['ip']} pair={p['pair'][0]} T={p['t'][0]} m={p['m'][0]}"
         if not isinstance(lib, str):
-            log(f"  skip {tag}: build failed: {str(lib).strip().splitlines()[-1][:120]}")
+            log(f"  skip {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]}: build failed: "
+                f"{str(lib).strip().splitlines()[-1][:120]}")
             continue
         try:
-            t = time_variant(lib, n, reps, side, psf, nspec)
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
         except Exception as e:  # a variant that does not launch (resources) is skipped
-            log(f"  skip {tag}: {str(e).splitlines()[-1][:120]}")
+            log(f"  skip {p['radices']} upb={p['upb'][0]} minb={p['minb'][0]} kstage={p['kstage']}: "
+                f"{str(e).splitlines()[-1][:120]}")
             continue
         results.append((p, t))
-        log(f"  {tag}: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+        log(f"  {p['radices']} tt={p['tt']} pf={p['pf'][0]} upb={p['upb'][0]} minb={p['minb'][0]} kstage={int(p['kstage'])}: "
+            + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
     if not results:
         raise RuntimeError(f"no variant of {n} ran")
-    # per radix order: the best (pair, threads, blocks) of each pass; then the
-    # order with the best total
+    # per (radix plan, threads per transform): best knob per pass; then the
+    # combination with the best total
     best = None
-    for rs in sorted({tuple(p["ip"]) for p, _ in results}):
-        rr = [(p, t) for p, t in results if tuple(p["ip"]) == rs]
+    for r, tt in sorted({(tuple(p["radices"]), p["tt"]) for p, _ in results}):
+        rs = [(p, t) for p, t in results if tuple(p["radices"]) == r and p["tt"] == tt]
+        if not rs:
+            continue
         choice, total = {}, 0.0
-        for name in ("p1_rows", "p2_cols", "p3_rows"):
-            p, t = min(rr, key=lambda x: x[1][name])
+        for k, name in enumerate(("p1_rows", "p2_cols", "p3_rows")):
+            # fastest setting; among those within 1 % of it (a knob the
+            # timed workload does not exercise), the fewest resident blocks
+            # (highest register cap), fewest units per block, no staging
+            tbest = min(t[name] for _, t in rs)
+            near = [(p, t) for p, t in rs if t[name] <= tbest * 1.01]
+            p, t = min(near, key=lambda x: (x[0]["minb"][k], x[0]["upb"][k], x[0]["kstage"], x[1][name]))
             choice[name] = p
             total += t[name]
         if best is None or total < best[0]:
-            best = (total, rs, choice)
-    total, rs, choice = best
-    names = ("p1_rows", "p2_cols", "p3_rows")
-    v2 = dict(ip=list(rs), pair=[choice[k]["pair"][0] for k in names], t=[choice[k]["t"][0] for k in names],
-              m=[choice[k]["m"][0] for k in names], batch=True, tuned_total_us=total * 1e3)
-    log(f"N={n}: chose {v2} (sum of best passes {total * 1e3:.1f} us)")
+            best = (total, r, choice, tt)
+    total, r, choice, tt = best
+    out = dict(base)
+    out.update(radices=list(r), threads=tt or B.threads_for(n, r), tt=tt,
+               upb=[choice["p1_rows"]["upb"][0], choice["p2_cols"]["upb"][1], choice["p3_rows"]["upb"][2]],
+               minb=[choice["p1_rows"]["minb"][0], choice["p2_cols"]["minb"][1], choice["p3_rows"]["minb"][2]],
+               kstage=choice["p2_cols"]["kstage"], tuned_total_us=total * 1e3,
+               pf=[choice["p1_rows"]["pf"][0], choice["p2_cols"]["pf"][1], choice["p3_rows"]["pf"][2]])
+    log(f"N={n}: chose {out['radices']} tt={out['tt']} pf={out['pf']} upb={out['upb']} minb={out['minb']} kstage={out['kstage']} "
+        f"(sum of best passes {total * 1e3:.1f} us)")
+    # refinement: double-buffered exchange on top of the choice, with each
+    # resident-block setting; kept per pass where it is faster
+    best_pass = {name: min(t[name] for p, t in results if tuple(p["radices"]) == tuple(out["radices"])
+                           and p["tt"] == out["tt"] and p["upb"][i] == out["upb"][i] and p["pf"][i] == out["pf"][i]
+                           and p["minb"][i] == out["minb"][i] and (i != 1 or p["kstage"] == out["kstage"]))
+                 for i, name in enumerate(("p1_rows", "p2_cols", "p3_rows"))}
+    refine = []
+    for minb in (1, 2, 3):
+        p = dict(out)
+        p.update(db=[1, 1, 1], minb=[minb] * 3)
+        refine.append(p)
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        rlibs = list(ex.map(build_or_error, refine))
+    db, minb = [0, 0, 0], list(out["minb"])
+    for p, lib in zip(refine, rlibs):
+        if not isinstance(lib, str):
+            continue
+        try:
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
+        except Exception as e:
+            log(f"  skip db=1 minb={p['minb'][0]}: {str(e).splitlines()[-1][:120]}")
+            continue
+        log(f"  db=1 minb={p['minb'][0]}: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+        for i, name in enumerate(("p1_rows", "p2_cols", "p3_rows")):
+            if t[name] < best_pass[name] * 0.99:
+                best_pass[name] = t[name]
+                db[i], minb[i] = 1, p["minb"][0]
+    out.update(db=db, minb=minb, tuned_total_us=sum(best_pass.values()) * 1e3)
+    log(f"N={n}: refined db={db} minb={minb} (sum {out['tuned_total_us']:.1f} us)")
     if nspec > 1:
-        p = dict(base)
-        p.update(v2, batch=False)
+        # several spectra: the batched column kernel against one single-
+        # spectrum pass per spectrum
+        p = dict(out, batch=False)
         lib = build_or_error(p)
         if isinstance(lib, str):
             try:
-                t = time_variant(lib, n, reps, side, psf, nspec)
+                t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
                 log(f"  batch=0: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
-                pbest = min(t2["p2_cols"] for p2, t2 in results if tuple(p2["ip"]) == rs)
-                if t["p2_cols"] < pbest * 0.99:
-                    v2["batch"] = False
+                if t["p2_cols"] < best_pass["p2_cols"] * 0.99:
+                    best_pass["p2_cols"] = t["p2_cols"]
+                    out.update(batch=False, tuned_total_us=sum(best_pass.values()) * 1e3)
             except Exception as e:
                 log(f"  skip batch=0: {str(e).splitlines()[-1][:120]}")
-        log(f"N={n}: batch={v2['batch']}")
-    return v2
+        log(f"N={n}: batch={out.get('batch', True)} (sum {out['tuned_total_us']:.1f} us)")
+    return out
 
 
 def main() -> None:
@@ -259,7 +301,7 @@ def main() -> None:
     ap.add_argument("--out", default=TUNED_JSON)
     ap.add_argument("--log", default=None)
     ap.add_argument("--plan", action="append", default=[],
-                    help="radix sequence to try, e.g. 12,8,7,7 (repeatable; default: the candidate list)")
+                    help="radix sequence to try, e.g. 7,7,8,12 (repeatable; default: the candidate list)")
     ap.add_argument("--psf", type=int, default=0, help="PSF side of the timed maps (default min(541, N/8))")
     ap.add_argument("--nspec", type=int, default=1, help="spectra per timed map (one forward transform)")
     ap.add_argument("--map-side", type=int, default=0,
@@ -280,7 +322,7 @@ def main() -> None:
             raise SystemExit(f"{n} is not in the supported size list")
     plans = [tuple(int(x) for x in p.split(",")) for p in args.plan]
     for p in plans:
-        if len(args.sizes) != 1 or _prod(p) != args.sizes[0] or max(p) > 16:
+        if len(args.sizes) != 1 or _prod(p) != args.sizes[0] or max(p) > 32:
             raise SystemExit(f"plan {p} is not a radix sequence of length {args.sizes}")
     common = _compile_common(jobs)
     table = {}
@@ -288,9 +330,8 @@ def main() -> None:
         with open(args.out) as fh:
             table = json.load(fh)
     for n in args.sizes:
-        v2 = tune_size(n, args.quick, jobs, common, log, args.map_side, args.psf, args.nspec, plans)
-        v2["tuned_on"] = {"map_side": args.map_side, "psf": args.psf, "nspec": args.nspec}
-        table.setdefault(str(n), {})["v2"] = v2
+        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side, args.psf, args.nspec, plans)
+        table[str(n)]["tuned_on"] = {"map_side": args.map_side, "psf": args.psf, "nspec": args.nspec}
         with open(args.out, "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
     log(f"wrote {args.out}")

