@@ -14,7 +14,6 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import hashlib
-import itertools
 import json
 import os
 import shutil
@@ -97,134 +96,6 @@ def choose_plan(n: int) -> Tuple[int, ...]:
 
 TUNED_JSON = os.path.join(HERE, "tuned_plans.json")
 
-# ---------------------------------------------------------------------------
-# Plans of the in-place engine (fft2.cuh)
-# ---------------------------------------------------------------------------
-IP_RADICES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16)
-IP_MAX_STAGES = 6
-SMEM_SM = 233472          # shared memory per SM (bytes)
-# FP32 lane operations per complex point of the in-register DFT of radix R
-# (FMA counted once), from the algorithms of fft2.cuh
-DFT_COST = {2: 2.0, 3: 4.7, 4: 4.0, 5: 7.2, 6: 6.7, 7: 9.4, 8: 7.3, 9: 11.1, 10: 9.2,
-            12: 8.7, 14: 11.4, 15: 11.9, 16: 9.9}
-TW_COST = 4.0             # per twiddled point
-STAGE_COST = 2.0          # shared-memory load + store per point and stage
-
-
-def _ip_factorizations(n: int) -> List[Tuple[int, ...]]:
-    out: List[Tuple[int, ...]] = []
-
-    def rec(rem: int, cur: List[int]) -> None:
-        if rem == 1:
-            if len(cur) >= 2:
-                out.append(tuple(cur))
-            return
-        if len(cur) == IP_MAX_STAGES:
-            return
-        for r in IP_RADICES:
-            if rem % r == 0:
-                rec(rem // r, cur + [r])
-
-    rec(n, [])
-    return out
-
-
-def _ip_geom(n: int, rs: Sequence[int]):
-    B, out = n, []
-    for r in rs:
-        out.append((r, B, B // r))   # radix, block size, stride
-        B //= r
-    return out
-
-
-def _ip_conflict(n: int, rs: Sequence[int], esize: int) -> float:
-    """Mean shared-memory wavefronts per access of the in-place stages, for
-    the thread-to-butterfly order of fft2.cuh (consecutive j, or
-    consecutive blocks when the stride is small and the block size odd)."""
-    per = 8 if esize == 16 else 16      # threads per access phase
-    slots = 128 // esize
-    tot, cnt = 0.0, 0
-    for (r, B, D) in _ip_geom(n, rs):
-        nblk = n // B
-        jfast = D >= 8 or (B % 2 == 0 and D > 1)
-        nb = n // r
-        worst = []
-        for ph in range(0, min(nb, 256), per):
-            seen: Dict[int, int] = {}
-            for b in range(ph, min(ph + per, nb)):
-                if jfast:
-                    j, blk = b % D, b // D
-                else:
-                    j, blk = b // nblk, b % nblk
-                a = (blk * B + j) % slots
-                seen[a] = seen.get(a, 0) + 1
-            worst.append(max(seen.values()))
-        tot += sum(worst) / len(worst)
-        cnt += 1
-    return tot / cnt
-
-
-def ip_cost(n: int, rs: Sequence[int], esize: int) -> float:
-    """Model cost per point of one transform (arithmetic + shared-memory
-    passes weighted by bank conflicts)."""
-    c = 0.0
-    for i, r in enumerate(rs):
-        c += DFT_COST[r] + STAGE_COST
-        if i < len(rs) - 1:
-            c += TW_COST * (r - 1) / r
-    return c + STAGE_COST * (_ip_conflict(n, rs, esize) - 1.0) * len(rs)
-
-
-def ip_regs(rs: Sequence[int], pair: bool) -> int:
-    return (4 if pair else 2) * max(rs) + 34
-
-
-def ip_launch(n: int, rs: Sequence[int], pair: bool) -> Tuple[int, int, float]:
-    """Threads per block and minimum resident blocks per SM for a plan:
-    balance of the butterflies over the threads (every stage), times an
-    occupancy factor."""
-    esize = 16 if pair else 8
-    smem = n * esize
-    best = None
-    regs = ip_regs(rs, pair)
-    for T in range(64, 1025, 32):
-        by_regs = 65536 // (T * ((regs + 7) // 8 * 8))
-        blocks = min(by_regs, SMEM_SM // (smem + 1024), 2048 // T, 32)
-        if blocks < 1:
-            continue
-        nbs = [n // r for r in rs]
-        es = [(x + T - 1) // T for x in nbs]
-        eff = sum(nbs) / (T * sum(es))
-        warps = blocks * T // 32
-        occ = min(1.0, warps / 20.0)
-        score = eff * occ
-        if best is None or score > best[0] + 1e-9:
-            best = (score, T, blocks)
-    if best is None:
-        raise ValueError(f"no launch shape for {n} {rs}")
-    return best[1], best[2], best[0]
-
-
-def ip_plan(n: int) -> dict:
-    """Plan of the in-place engine for length n: two transforms per block
-    where two blocks of them fit an SM's shared memory, else one; radices
-    (DIF order, each <= 16) of least modelled cost; threads per block."""
-    pair = 16 * n + 1024 <= SMEM_SM // 2
-    if 8 * n + 1024 > SMEM_SM:
-        raise ValueError(f"length {n} does not fit shared memory")
-    esize = 16 if pair else 8
-    best = None
-    for f in _ip_factorizations(n):
-        for perm in set(itertools.permutations(f)):
-            c = ip_cost(n, perm, esize)
-            T, blocks, score = ip_launch(n, perm, pair)
-            total = c / max(score, 1e-3)
-            key = (total, len(perm), -perm[-1] % 2)
-            if best is None or key < best[0]:
-                best = (key, perm, T, blocks)
-    _, rs, T, blocks = best
-    return dict(ip=list(rs), pair=[int(pair)] * 3, t=[T] * 3, m=[blocks] * 3, batch=True)
-
 
 def plan_table_entry(n: int) -> dict:
     """Heuristic plan of one length (used when the autotuner has not
@@ -274,28 +145,31 @@ def plan_table() -> Dict[int, dict]:
 
 
 _SIZE_TU = """// generated by paper_1907_02891_gb300/build.py -- one supported FFT length
-#include "conv2.cuh"
+#include "conv_kernels.cuh"
 #include "lp_internal.h"
 #include "tc_kernels.cuh"
 
 namespace lpk {{
 namespace {{
 constexpr int kN = {n};
-// in-place engine: radices in forward (DIF) order
-using G = IpGeom<kN, {ipseq}>;
-// per pass (row forward, column, row inverse): threads per block, minimum
-// resident blocks per SM (register cap), two transforms per block or one
-constexpr int kT1 = {t1}, kT2 = {t2}, kT3 = {t3};
-constexpr int kM1 = {m1}, kM2 = {m2}, kM3 = {m3};
-using C1 = {c1};
-using C2 = {c2};
-using C3 = {c3};
-// several spectra: one forward column transform for all (parked) or one
-// single-spectrum column pass per spectrum
+using P = Plan<kN, Seq<{seq}>, {tt}>;   // threads per transform (0 = one butterfly each)
+constexpr int kF1 = {f1}, kF3 = {f3};
+constexpr int kSmem = P::SMEM_BYTES;
+constexpr int kSmem2 = P::SMEM_BYTES + 8 * kN;   // + a parked column (batched / multi-class)
+constexpr long long kMaxSmem = 227 * 1024;
+// tuned parameters of the prefetching kernels: work units per block and
+// minimum resident blocks per SM (register cap) per pass; spectrum staging
+constexpr int kUPB1 = {upb1}, kUPB2 = {upb2}, kUPB3 = {upb3};
+constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
+constexpr bool kKSTAGE = {kstage};
+constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
+constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
+// several spectra: the batched column kernel (forward column parked in shared
+// memory, one product + inverse per spectrum) or one single-spectrum pass per
+// spectrum (forward transform repeated)
 constexpr bool kBatch = {batch};
-constexpr int kSm1 = kN * (int)sizeof(C1), kSm2 = kN * (int)sizeof(C2), kSm3 = kN * (int)sizeof(C3);
-// split-precision tensor-core column pass: its own Stockham radix plan
-using P = Plan<kN, Seq<{seq}>, {tt}>;
+constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
+// split-precision tensor-core column pass (0 shared bytes: not available)
 using TP = TcPlan<P, kN>;
 constexpr bool kTC = TP::FITS;
 constexpr int kTcSmem = kTC ? TP::SMEM_BYTES : 0;
@@ -306,62 +180,80 @@ cudaError_t attr(K k, int bytes)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }}
 
+// blocks of a prefetching launch: each block takes upb units
+inline int persistent_grid(int units, int upb) {{ return (units + upb - 1) / upb; }}
+
 cudaError_t set_attrs()
 {{
     cudaError_t e;
-    if ((e = attr(p1v2<G, kT1, kM1, C1>, kSm1)) != cudaSuccess) return e;
-    if ((e = attr(p2v2<G, kT2, kM2, C2, true>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p2v2<G, kT2, kM2, C2, false>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p2v2_multi<G, kT2, kM2, C2, true>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p2v2_multi<G, kT2, kM2, C2, false>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p2v2_multiclass<G, kT2, kM2, C2, true>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p2v2_multiclass<G, kT2, kM2, C2, false>, kSm2)) != cudaSuccess) return e;
-    if ((e = attr(p3v2<G, kT3, kM3, C3>, kSm3)) != cudaSuccess) return e;
+    if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
+    if constexpr (kSmem2 <= kMaxSmem) {{
+        if ((e = attr(p2_cols<P, kN, true, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_cols<P, kN, false, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_multiclass<P, kN, true>, kSmem2)) != cudaSuccess) return e;
+        if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
+    }}
+    if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
     if constexpr (kTC) {{
         if ((e = attr(p2_cols_tc<P, kN, true>, kTcSmem)) != cudaSuccess) return e;
         if ((e = attr(p2_cols_tc<P, kN, false>, kTcSmem)) != cudaSuccess) return e;
     }}
-    return cudaSuccess;
+    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    return attr(p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3>, (int)kMaxSmem);
 }}
 
-cudaError_t p1(const P1v2Args& a, cudaStream_t s)
+cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
-    return launch_pdl(p1v2<G, kT1, kM1, C1>, dim3(a.units - a.unit0), dim3(kT1), kSm1, s, a);
+    const long long sm = kX1 * kSmem + p1_stage_bytes(a.Wst);
+    if (kPF1 && sm <= kMaxSmem)
+        return launch_pdl(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, dim3(persistent_grid(a.npairs - a.pair0, kUPB1)),
+                          dim3(P::T), sm, s, a);
+    return launch_pdl(p1_rows<P, kN, kF1>, dim3((a.npairs - a.pair0 + kF1 - 1) / kF1), dim3(P::T * kF1),
+                      kF1 * kSmem, s, a);
 }}
 
-// units of the column pass: column pairs (two transforms) or columns
-inline int col_units(int ncols) {{ return std::is_same<C2, CP>::value ? (ncols + 1) / 2 : ncols; }}
-
-cudaError_t p2(const P2v2Args& a, bool kreal, cudaStream_t s)
+cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 {{
-    const dim3 g(col_units(a.ncols));
-    if (a.nspec == 1)
-        return kreal ? launch_pdl(p2v2<G, kT2, kM2, C2, true>, g, dim3(kT2), kSm2, s, a)
-                     : launch_pdl(p2v2<G, kT2, kM2, C2, false>, g, dim3(kT2), kSm2, s, a);
-    if (kBatch && a.park)
-        return kreal ? launch_pdl(p2v2_multi<G, kT2, kM2, C2, true>, g, dim3(kT2), kSm2, s, a)
-                     : launch_pdl(p2v2_multi<G, kT2, kM2, C2, false>, g, dim3(kT2), kSm2, s, a);
-    for (int i = 0; i < a.nspec; ++i) {{
-        P2v2Args b = a;
-        b.K[0] = a.K[i];
-        b.nspec = 1;
-        b.U = a.U + (long long)i * a.specU;
-        cudaError_t e = p2(b, kreal, s);
-        if (e != cudaSuccess) return e;
+    const bool multi = a.nspec > 1;
+    const long long sm = kX2 * kSmem + p2_stage_bytes(a.ldT, a.ldK, kreal, kKSTAGE);
+    if (!multi) {{
+        const dim3 gpf(persistent_grid(a.ncols, kUPB2));
+        if (kPF2 && sm <= kMaxSmem)
+            return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a)
+                         : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a);
+        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a);
     }}
-    return cudaSuccess;
+    if constexpr (kBatch && kSmem2 <= kMaxSmem) {{
+        return kreal ? launch_pdl(p2_cols<P, kN, true, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
+    }} else {{
+        // one single-spectrum pass per spectrum (no room to park the forward
+        // column, or the plan measured this faster)
+        for (int i = 0; i < a.nspec; ++i) {{
+            P2Args b = a;
+            b.K[0] = a.K[i];
+            b.nspec = 1;
+            b.U = a.U + (long long)i * a.specU;
+            cudaError_t e = p2(b, kreal, s);
+            if (e != cudaSuccess) return e;
+        }}
+        return cudaSuccess;
+    }}
 }}
 
-cudaError_t p2m(const P2Mv2Args& m, bool kreal, cudaStream_t s)
+cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 {{
-    const dim3 g(col_units(m.a.ncols));
-    return kreal ? launch_pdl(p2v2_multiclass<G, kT2, kM2, C2, true>, g, dim3(kT2), kSm2, s, m)
-                 : launch_pdl(p2v2_multiclass<G, kT2, kM2, C2, false>, g, dim3(kT2), kSm2, s, m);
-}}
-
-cudaError_t p3(const P3v2Args& a, int nspec, cudaStream_t s)
-{{
-    return launch_pdl(p3v2<G, kT3, kM3, C3>, dim3(a.units - a.unit0, nspec), dim3(kT3), kSm3, s, a);
+    if constexpr (kSmem2 <= kMaxSmem) {{
+        return kreal ? launch_pdl(p2_multiclass<P, kN, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
+                     : launch_pdl(p2_multiclass<P, kN, false>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
+    }} else {{
+        return cudaErrorNotSupported;
+    }}
 }}
 
 // persistent grid of the tensor-core column pass: resident blocks per SM
@@ -402,11 +294,21 @@ cudaError_t p2tc(const P2TcArgs& a, bool kreal, cudaStream_t s)
         return cudaErrorNotSupported;
     }}
 }}
+
+cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
+{{
+    const long long sm = kX3 * kSmem + p3_stage_bytes(a.ncols);
+    if (kPF3 && sm <= kMaxSmem)
+        return launch_pdl(p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3>, dim3(persistent_grid(a.npairs - a.pair0, kUPB3), nspec),
+                          dim3(P::T), sm, s, a);
+    return launch_pdl(p3_rows<P, kN, kF3>, dim3((a.npairs - a.pair0 + kF3 - 1) / kF3, nspec), dim3(P::T * kF3),
+                      kF3 * kSmem, s, a);
+}}
 }}  // namespace
 
-extern const SizeKernels kSize_{n} = {{kN, {ipns}, {{{iprad8}}}, {{{pairs}}}, {{kT1, kT2, kT3}}, kBatch ? 1 : 0,
+extern const SizeKernels kSize_{n} = {{kN, {ns}, {{{rad6}}}, P::T, kF1, kF3, kSmem,
                                        set_attrs, p1, p2, p2m, p3,
-                                       {ns}, {{{rad6}}}, kTC ? TP::THREADS : 0, kTcSmem, p2tc}};
+                                       kTC ? TP::THREADS : 0, kTcSmem, p2tc}};
 }}  // namespace lpk
 """
 

@@ -209,7 +209,7 @@ __device__ __forceinline__ void spectrum_product(float2 (&f)[P::EL][P::RL], int 
             const int u = j + m * NBL;
             if constexpr (KREAL) {
                 const float k = STAGED ? kst[u] : __ldg(static_cast<const float*>(kcol) + u);
-                f[e][m] = make_float2(f[e][m].x * k, f[e][m].y * k);
+                f[e][m] = cscale(f[e][m], k);
             } else {
                 const float2 k = STAGED ? reinterpret_cast<const float2*>(kst)[u]
                                         : __ldg(static_cast<const float2*>(kcol) + u);

@@ -115,6 +115,32 @@ __device__ __forceinline__ C mk(typename Scalar<C>::type x, typename Scalar<C>::
 }
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// a * c (c real) and a * c + acc
+template <class C> __device__ __forceinline__ C cscale(C a, typename Scalar<C>::type c)
+{
+    return mk<C>(a.x * c, a.y * c);
+}
+template <class C> __device__ __forceinline__ C cfma(C a, typename Scalar<C>::type c, C acc)
+{
+    return mk<C>(a.x * c + acc.x, a.y * c + acc.y);
+}
+
+// FP32 complex values {re, im} are a natural pair for the packed FP32x2
+// instructions: an addition, a subtraction, a real scaling or a real
+// multiply-add of a complex value is one add / sub / mul / fma .f32x2.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+__device__ __forceinline__ float2 cscale(float2 a, float c) { return __fmul2_rn(a, make_float2(c, c)); }
+__device__ __forceinline__ float2 cfma(float2 a, float c, float2 acc) { return __ffma2_rn(a, make_float2(c, c), acc); }
 template <class C> __device__ __forceinline__ C cmul(C a, C b)
 {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -236,15 +262,13 @@ __device__ __forceinline__ void dft_odd_prime(C* v)
     sfor<1, H + 1>([&](auto M_) {
         constexpr int m = decltype(M_)::value;
         C re = v[0];
-        C im = mk<C>((S)0, (S)0);
+        C im;
         sfor<1, H + 1>([&](auto K_) {
             constexpr int k = decltype(K_)::value;
             constexpr S c = (S)cos2pi((long)k * m, P);
             constexpr S s = (S)sin2pi((long)k * m, P);
-            re.x += a[k - 1].x * c;
-            re.y += a[k - 1].y * c;
-            im.x += b[k - 1].x * s;
-            im.y += b[k - 1].y * s;
+            re = cfma(a[k - 1], c, re);
+            im = (k == 1) ? cscale(b[0], s) : cfma(b[k - 1], s, im);
         });
         // y_m = re + DIR i im ; y_{P-m} = re - DIR i im
         C ii = mul_idir<DIR>(im);
