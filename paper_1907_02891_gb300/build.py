@@ -137,7 +137,8 @@ def plan_table() -> Dict[int, dict]:
             e.update(radices=list(t["radices"]), threads=threads_for(n, t["radices"]),
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
                      tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
-                     db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)))
+                     db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)),
+                     minbm=int(t.get("minbm", 2)), kst2=bool(t.get("kst2", True)))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -168,6 +169,11 @@ constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered ex
 // memory, one product + inverse per spectrum) or one single-spectrum pass per
 // spectrum (forward transform repeated)
 constexpr bool kBatch = {batch};
+// minimum resident blocks per SM of the batched column kernel
+constexpr int kMINBM = {minbm};
+// one-unit-per-block column kernel: spectrum column staged in shared memory
+constexpr bool kKST2 = {kst2};
+constexpr int kKst(bool kreal) {{ return kKST2 ? (kreal ? 4 : 8) * ((kN + 3) / 4 * 4) : 0; }}
 constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
 // split-precision tensor-core column pass (0 shared bytes: not available)
 using TP = TcPlan<P, kN>;
@@ -187,11 +193,11 @@ cudaError_t set_attrs()
 {{
     cudaError_t e;
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2>, kX2 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKST2>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKST2>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, true, kMINBM>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, true, kMINBM>, kSmem)) != cudaSuccess) return e;
     if constexpr (kSmem2 <= kMaxSmem) {{
-        if ((e = attr(p2_cols<P, kN, true, true>, kSmem2)) != cudaSuccess) return e;
-        if ((e = attr(p2_cols<P, kN, false, true>, kSmem2)) != cudaSuccess) return e;
         if ((e = attr(p2_multiclass<P, kN, true>, kSmem2)) != cudaSuccess) return e;
         if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
     }}
@@ -225,12 +231,14 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
         if (kPF2 && sm <= kMaxSmem)
             return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a)
                          : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a);
-        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a)
-                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2>, dim3(a.ncols), dim3(P::T), kX2 * kSmem, s, a);
+        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2, kKST2>, dim3(a.ncols), dim3(P::T),
+                                  kX2 * kSmem + kKst(true), s, a)
+                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKST2>, dim3(a.ncols), dim3(P::T),
+                                  kX2 * kSmem + kKst(false), s, a);
     }}
-    if constexpr (kBatch && kSmem2 <= kMaxSmem) {{
-        return kreal ? launch_pdl(p2_cols<P, kN, true, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
-                     : launch_pdl(p2_cols<P, kN, false, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
+    if (kBatch && a.park) {{
+        return kreal ? launch_pdl(p2_cols<P, kN, true, true, kMINBM>, dim3(a.ncols), dim3(P::T), kSmem, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, true, kMINBM>, dim3(a.ncols), dim3(P::T), kSmem, s, a);
     }} else {{
         // one single-spectrum pass per spectrum (no room to park the forward
         // column, or the plan measured this faster)
@@ -306,7 +314,7 @@ cudaError_t p3(const P3Args& a, int nspec, cudaStream_t s)
 }}
 }}  // namespace
 
-extern const SizeKernels kSize_{n} = {{kN, {ns}, {{{rad6}}}, P::T, kF1, kF3, kSmem,
+extern const SizeKernels kSize_{n} = {{kN, {ns}, {{{rad6}}}, P::T, kF1, kF3, kSmem, kBatch ? 1 : 0,
                                        set_attrs, p1, p2, p2m, p3,
                                        kTC ? TP::THREADS : 0, kTcSmem, p2tc}};
 }}  // namespace lpk
@@ -349,7 +357,8 @@ def generate() -> List[str]:
                                kstage="true" if p["kstage"] else "false",
                                pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
                                db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
-                               batch=_b(p.get("batch", True)),
+                               batch=_b(p.get("batch", True)), minbm=p.get("minbm", 2),
+                               kst2=_b(p.get("kst2", True)),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

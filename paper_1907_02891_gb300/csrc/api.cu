@@ -789,12 +789,24 @@ static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mo
     }
     d->ldU = even_up(d->Hout);
     d->prec = (int)LP_PREC_FP32;
+    d->ny = ny;
+    const SizeKernels* k = find_size(ny);
+    d->batch = (k && k->batch) ? 1 : 0;
+}
+
+size_t lp_park_bytes(const MapDims& d) { return 8ull * (size_t)d.ncols * (size_t)d.ny; }
+
+// the batched column pass parks its forward column spectra in the workspace
+static inline bool uses_park(const MapDims& d, int nchunk)
+{
+    return nchunk > 1 && d.batch && d.prec == (int)LP_PREC_FP32;
 }
 
 size_t lp_workspace_bytes(const MapDims& d, int n)
 {
     const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
-    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) + 256;
+    return 8ull * ((size_t)d.ncolsT * (size_t)d.ldT + (size_t)d.ncolsU * (size_t)nchunk * (size_t)d.ldU) +
+           (uses_park(d, nchunk) ? lp_park_bytes(d) + 256 : 0) + 256;
 }
 
 extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, int wk, int n,
@@ -869,7 +881,8 @@ static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float
 
 // column pass for spectra [base, base+cnt) into U (cnt blocks of ncols x ldU)
 static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectrum* const* spectra, int base,
-                                int cnt, int h, const MapDims& d, const float2* T, float2* U, cudaStream_t st)
+                                int cnt, int h, const MapDims& d, const float2* T, float2* U, float2* park,
+                                cudaStream_t st)
 {
     const lp_spectrum* s0 = spectra[0];
     if (d.prec == (int)LP_PREC_SPLIT_BF16) {
@@ -893,6 +906,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.ncols = d.ncols;
             b.twf = py->fwd;
             b.twi = py->rev;
+            b.park = nullptr;
             a2.tables = static_cast<const uint4*>(py->tc_tables);
             a2.err = ctx->d_err;
             a2.no_mma = (ctx->test_hook & LP_TEST_TC_NO_MMA) ? 1 : 0;
@@ -926,6 +940,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
         a2.ncols = d.ncols;
         a2.twf = py->fwd;
         a2.twi = py->rev;
+        a2.park = park;
         const int tok = lp_pass_begin(ctx, 1, st);
         CUDA_TRY(py->k->p2(a2, kind != 0, st));
         lp_pass_end(ctx, tok, st);
@@ -956,6 +971,13 @@ static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDi
     return LP_OK;
 }
 
+// park area after U in a workspace (256-byte aligned)
+static inline float2* park_of(const MapDims& d, float2* U, int nchunk)
+{
+    const uintptr_t p = reinterpret_cast<uintptr_t>(U + (size_t)d.ncolsU * d.ldU * (size_t)nchunk);
+    return reinterpret_cast<float2*>((p + 255) / 256 * 256);
+}
+
 // Launch P1, P2, P3 for n spectra (the validated sequence of lp_map).
 lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
@@ -969,11 +991,13 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     if (ps != LP_OK) return ps;
     float2* T = static_cast<float2*>(ws);
     float2* U = T + (size_t)d.ncolsT * d.ldT;
+    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
+    float2* park = uses_park(d, nchunk) ? park_of(d, U, nchunk) : nullptr;
     if ((ps = lp_wait_spectra_built(spectra, n, st)) != LP_OK) return ps;
     if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
-        if ((ps = launch_columns(ctx, py, spectra, base, cnt, h, d, T, U, st)) != LP_OK) return ps;
+        if ((ps = launch_columns(ctx, py, spectra, base, cnt, h, d, T, U, park, st)) != LP_OK) return ps;
         if ((ps = launch_rows_inverse(ctx, px, d, U, cnt, out + base, ldo, 0, (int)(d.ldU / 2), st)) != LP_OK)
             return ps;
     }
@@ -1098,6 +1122,8 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     if (st != LP_OK) return st;
     float2* T = static_cast<float2*>(ws);
     float2* U = T + (size_t)d.ncolsT * d.ldT;
+    const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
+    float2* park = uses_park(d, nchunk) ? park_of(d, U, nchunk) : nullptr;
     cudaEvent_t* ev = ctx->hs_events.data();
     cudaEvent_t ev_start = ev[0], ev_end = ev[1];
     cudaEvent_t* ev_in = ev + 2;                 // kHostBands
@@ -1137,7 +1163,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     const int nb_out = host_bands(obytes * (size_t)n, opairs);
     for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {
         const int cnt = (n - cb) < kMaxSpectraPerLaunch ? (n - cb) : kMaxSpectraPerLaunch;
-        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, c)) != LP_OK) return st;
+        if ((st = launch_columns(ctx, py, spectra, cb, cnt, h, d, T, U, park, c)) != LP_OK) return st;
         if (cb == 0 && ctx->hs_ofree_valid[obuf]) CUDA_TRY(cudaStreamWaitEvent(c, ctx->hs_ofree[obuf], 0));
         for (int b = 0; b < nb_out; ++b) {
             const int q0 = (int)((long long)opairs * b / nb_out), q1 = (int)((long long)opairs * (b + 1) / nb_out);

@@ -112,6 +112,7 @@ struct P2Args {
     int HoutPad;      // 2 ceil(Hout/2): rows written (the extra one is zero)
     int ncols;
     TwChain twf, twi;  // forward and reversed chains of the column plan
+    float2* park;      // batched pass: forward column spectra, N per column
 };
 
 struct P3Args {
@@ -348,9 +349,9 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 // P2: per column forward FFT, spectrum product, inverse FFT, row crop.
 // ---------------------------------------------------------------------------
 // One spectrum of the batched column pass: the forward column is parked in
-// shared memory F (natural order); product with spectrum s, inverse, store.
-// Not inlined: as a loop body it would let the compiler keep the whole
-// inverse's constants and indices live across iterations.
+// F (natural order); product with spectrum s, inverse, store.  Not inlined:
+// as a loop body it would let the compiler keep the whole inverse's
+// constants and indices live across iterations.
 template <class P, int N, bool KREAL>
 __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, const float2* F, float2* sm)
 {
@@ -373,11 +374,21 @@ __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, con
     });
 }
 
-template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false>
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem);
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem);
+__device__ __forceinline__ void cp_async_commit();
+__device__ __forceinline__ void cp_async_wait_all();
+
+// KST (one spectrum): the block's spectrum column is copied into shared
+// memory (after the exchange buffer) with cp.async at the start, so its
+// load latency overlaps the forward transform instead of stalling the
+// product.
+template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false, bool KST = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2Args a)
 {
     pdl_begin();
     static_assert(!(DB && MULTI), "the batched column pass is single-buffered");
+    static_assert(!(KST && MULTI), "spectrum staging is for one spectrum");
     using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
     using Inv = typename std::conditional<DB, typename P::InvChainDB, typename P::InvChain>::type;
     extern __shared__ float2 smem2[];
@@ -387,6 +398,14 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     const int c = blockIdx.x;
     const int t = threadIdx.x;
     const float2* col = t_column(a.T, a.ldT, c);
+    constexpr int KW = KREAL ? 1 : 2;  // floats per spectrum value
+    float* kst = reinterpret_cast<float*>(smem2 + (DB ? 2 : 1) * P::SMEM_ELEMS);
+    if constexpr (KST) {
+        // ldK is a multiple of 32, so the column start is 16-byte aligned
+        const float* src = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
+        for (int q = t; q < (N * KW + 3) / 4; q += P::T) cp_async16(kst + 4 * q, src + 4 * q);
+        cp_async_commit();
+    }
 
     float2 v[P::E0][R0];
 #pragma unroll
@@ -402,7 +421,11 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     }
     Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
         if constexpr (MULTI) {
-            float2* F = smem2 + P::SMEM_ELEMS;  // parked forward column
+            // parked forward column in global memory (L2-resident while the
+            // block runs): each thread reads back only the elements it wrote,
+            // so no barrier orders the park; shared memory stays one exchange
+            // buffer, so more blocks fit an SM
+            float2* F = a.park + (size_t)c * N;
 #pragma unroll
             for (int e = 0; e < P::EL; ++e) {
                 const int j = tt + e * P::T;
@@ -412,9 +435,12 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
             }
             for (int s = 0; s < a.nspec; ++s) p2_spectrum_pass<P, N, KREAL>(a, c, s, F, sm);
         } else {
-            const long long kw = KREAL ? 1 : 2;
-            spectrum_product<P, N, KREAL, false>(fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * kw,
-                                                 nullptr);
+            if constexpr (KST) {
+                cp_async_wait_all();
+                __syncthreads();  // every thread's share of the column has landed
+            }
+            spectrum_product<P, N, KREAL, KST>(fz, tt, static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW,
+                                               kst);
             float2* Uc = u_column(a.U, a.ldU, c);
             Inv::run(fz, tt, sm, a.twi, [&](float2(&o)[P::EJ][R0], int t2) {
                 store_column<P, N>(o, t2, Uc, a.r0, a.Hout, a.HoutPad);

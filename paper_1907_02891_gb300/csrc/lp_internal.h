@@ -27,6 +27,7 @@ struct SizeKernels {
     int threads;         // threads per transform
     int f1, f3;          // transforms per block in the row passes
     int smem_bytes;      // dynamic shared memory of one transform
+    int batch;           // several spectra: one forward column transform, parked
     cudaError_t (*set_attrs)();
     // launchers: pick the persistent prefetching kernel when its shared
     // memory fits, the one-unit-per-block kernel otherwise

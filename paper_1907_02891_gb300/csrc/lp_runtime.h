@@ -52,6 +52,8 @@ struct MapDims {
     int Hout, Wout;     // output size
     int r0, c0;         // first kept row / column of the circular result
     int prec;           // lp_precision of the column pass
+    int ny;             // padded column length
+    int batch;          // several FP32 spectra share one forward column transform
 };
 
 struct ServeState;
@@ -128,6 +130,8 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
 // bytes of one map's workspace: T, then U for up to kMaxSpectraPerLaunch
 // spectra (the spectra of one launch), + alignment slack
 size_t lp_workspace_bytes(const MapDims& d, int n);
+// parked forward column spectra of the batched column pass: Ny complex per column
+size_t lp_park_bytes(const MapDims& d);
 lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                         const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                         const MapDims& d, void* ws, cudaStream_t st);
