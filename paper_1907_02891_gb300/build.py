@@ -156,7 +156,6 @@ constexpr int kN = {n};
 using P = Plan<kN, Seq<{seq}>, {tt}>;   // threads per transform (0 = one butterfly each)
 constexpr int kF1 = {f1}, kF3 = {f3};
 constexpr int kSmem = P::SMEM_BYTES;
-constexpr int kSmem2 = P::SMEM_BYTES + 8 * kN;   // + a parked column (batched / multi-class)
 constexpr long long kMaxSmem = 227 * 1024;
 // tuned parameters of the prefetching kernels: work units per block and
 // minimum resident blocks per SM (register cap) per pass; spectrum staging
@@ -165,16 +164,21 @@ constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
 constexpr bool kKSTAGE = {kstage};
 constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
 constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
-// several spectra: the batched column kernel (forward column parked in shared
+// several spectra: the batched column kernel (forward column parked in global
 // memory, one product + inverse per spectrum) or one single-spectrum pass per
 // spectrum (forward transform repeated)
 constexpr bool kBatch = {batch};
 // minimum resident blocks per SM of the batched column kernel
 constexpr int kMINBM = {minbm};
-// one-unit-per-block column kernel: spectrum column staged in shared memory
-constexpr bool kKST2 = {kst2};
-constexpr int kKst(bool kreal) {{ return kKST2 ? (kreal ? 4 : 8) * ((kN + 3) / 4 * 4) : 0; }}
 constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
+// one-unit-per-block column kernel: spectrum column staged in shared memory
+// (where the staging fits next to the exchange buffer)
+constexpr bool kKST2 = {kst2};
+constexpr bool kKstOk(bool kreal)
+{{
+    return kKST2 && (long long)kX2 * kSmem + (kreal ? 4 : 8) * ((kN + 3) / 4 * 4) <= kMaxSmem;
+}}
+constexpr int kKst(bool kreal) {{ return kKstOk(kreal) ? (kreal ? 4 : 8) * ((kN + 3) / 4 * 4) : 0; }}
 // split-precision tensor-core column pass (0 shared bytes: not available)
 using TP = TcPlan<P, kN>;
 constexpr bool kTC = TP::FITS;
@@ -193,14 +197,12 @@ cudaError_t set_attrs()
 {{
     cudaError_t e;
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKST2>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKST2>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true)>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, true, true, kMINBM>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, false, true, kMINBM>, kSmem)) != cudaSuccess) return e;
-    if constexpr (kSmem2 <= kMaxSmem) {{
-        if ((e = attr(p2_multiclass<P, kN, true>, kSmem2)) != cudaSuccess) return e;
-        if ((e = attr(p2_multiclass<P, kN, false>, kSmem2)) != cudaSuccess) return e;
-    }}
+    if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_multiclass<P, kN, false>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
     if constexpr (kTC) {{
         if ((e = attr(p2_cols_tc<P, kN, true>, kTcSmem)) != cudaSuccess) return e;
@@ -231,9 +233,9 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
         if (kPF2 && sm <= kMaxSmem)
             return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a)
                          : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a);
-        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2, kKST2>, dim3(a.ncols), dim3(P::T),
+        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true)>, dim3(a.ncols), dim3(P::T),
                                   kX2 * kSmem + kKst(true), s, a)
-                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKST2>, dim3(a.ncols), dim3(P::T),
+                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, dim3(a.ncols), dim3(P::T),
                                   kX2 * kSmem + kKst(false), s, a);
     }}
     if (kBatch && a.park) {{
@@ -256,12 +258,8 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
 
 cudaError_t p2m(const P2MArgs& a, bool kreal, cudaStream_t s)
 {{
-    if constexpr (kSmem2 <= kMaxSmem) {{
-        return kreal ? launch_pdl(p2_multiclass<P, kN, true>, dim3(a.ncols), dim3(P::T), kSmem2, s, a)
-                     : launch_pdl(p2_multiclass<P, kN, false>, dim3(a.ncols), dim3(P::T), kSmem2, s, a);
-    }} else {{
-        return cudaErrorNotSupported;
-    }}
+    return kreal ? launch_pdl(p2_multiclass<P, kN, true>, dim3(a.ncols), dim3(P::T), kSmem, s, a)
+                 : launch_pdl(p2_multiclass<P, kN, false>, dim3(a.ncols), dim3(P::T), kSmem, s, a);
 }}
 
 // persistent grid of the tensor-core column pass: resident blocks per SM

@@ -1254,9 +1254,11 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     const size_t tbytes = 8ull * (size_t)d.ncolsT * d.ldT;
     const size_t ubytes = 8ull * (size_t)d.ncolsU * d.ldU;
     void* ws = nullptr;
-    if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + 256, &ws)) != LP_OK) return st;
+    if ((st = lp_get_workspace(ctx, s, (size_t)T * tbytes + ubytes + lp_park_bytes(d) + 512, &ws)) != LP_OK)
+        return st;
     float2* Tb = static_cast<float2*>(ws);
     float2* U = Tb + (size_t)T * d.ncolsT * d.ldT;
+    float2* accb = park_of(d, U, 1);
     const int npairs = (int)(d.ldT / 2);
     if ((st = lp_wait_spectra_built(spectra, T, s)) != LP_OK) return st;
     for (int t = 0; t < T; ++t) {
@@ -1300,12 +1302,9 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a2.ncols = d.ncols;
     a2.twf = py->fwd;
     a2.twi = py->rev;
+    a2.acc = accb;
     {
         const cudaError_t e = py->k->p2m(a2, all_real, s);
-        if (e == cudaErrorNotSupported)
-            return lp_fail(LP_ERR_UNSUPPORTED,
-                           "lp_map_multiclass: padded length %d leaves no shared memory for the "
-                           "class accumulator (supported up to about 14000)", s0->ny);
         if (e != cudaSuccess) return lp_fail(LP_ERR_CUDA, "lp_map_multiclass: %s", cudaGetErrorString(e));
     }
     P3Args a3;

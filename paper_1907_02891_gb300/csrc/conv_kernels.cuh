@@ -725,11 +725,14 @@ struct P2MArgs {
     int r0, Hout, HoutPad;
     int ncols;
     TwChain twf, twi;
+    float2* acc;  // the sums of the products, N per column (global memory)
 };
 
 // One class of the Eq. (4) column pass: forward transform of the class's
-// column, product with its spectrum, accumulated into shared memory ACC
-// (natural order).  Not inlined, for the same reason as p2_spectrum_pass.
+// column, product with its spectrum, summed into ACC (natural order; the
+// first class writes it).  Each thread adds only to the elements it owns
+// (j + m N/RL), so the sum needs no barrier.  Not inlined, for the same
+// reason as p2_spectrum_pass.
 template <class P, int N, bool KREAL>
 __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float2* ACC, float2* sm)
 {
@@ -760,7 +763,7 @@ __device__ __noinline__ void p2_class_pass(const P2MArgs& a, int c, int q, float
 #pragma unroll
             for (int m = 0; m < RL; ++m) {
                 float2& acc = ACC[j + m * NBL];
-                acc = cadd(acc, fz[e][m]);
+                acc = q == 0 ? fz[e][m] : cadd(acc, fz[e][m]);
             }
         }
     });
@@ -773,16 +776,14 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2
     extern __shared__ float2 smem2[];
     constexpr int RL = P::RL, NBL = N / RL;
     float2* sm = smem2;
-    float2* ACC = smem2 + P::SMEM_ELEMS;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
-
-    for (int i = t; i < N; i += blockDim.x) ACC[i] = make_float2(0.f, 0.f);
-    // every element of ACC is owned by one thread (j + m N/RL), so the
-    // accumulation needs no barrier; the chain's own barriers order sm and
-    // the initialisation above
+    // the sums live in global memory (L2-resident while the block runs), so
+    // shared memory holds one exchange buffer at every length; every
+    // element of ACC is owned by one thread (j + m N/RL), which writes it for
+    // the first class, adds to it for the others and reads it back below
+    float2* ACC = a.acc + (size_t)c * N;
     for (int q = 0; q < a.nclass; ++q) p2_class_pass<P, N, KREAL>(a, c, q, ACC, sm);
-    __syncthreads();
     float2 acc[P::EL][RL];
 #pragma unroll
     for (int e = 0; e < P::EL; ++e) {

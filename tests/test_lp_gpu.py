@@ -400,6 +400,29 @@ def test_multiclass_eq4_at_workload_size(ctx):
         lp.lp_spectrum_release(ctx, s)
 
 
+def test_multiclass_eq4_at_the_longest_column_length(ctx):
+    """Eq. (4) with the column transform at 17280 (the longest built length;
+    the sums of the class products live in global memory, so every length
+    takes several classes): a tall 16384 x 64 map per class, 31 x 31 PSFs,
+    sampled against the oracle."""
+    H, W = 16384, 64
+    Ls = [synth.radiance_map(H, W, 200, 1907_02891 + 50 + t, lit_fraction=0.05) for t in range(3)]
+    Ks = [synth.psf_power_exp(31, 1.0, 0.25, p, 40.0) for p in (1.0, 1.5, 2.0)]
+    specs = [lp.lp_kernel_spectrum(ctx, dev(K), pad_ny=17280, pad_nx=96) for K in Ks]
+    out = torch.empty((H, W), dtype=torch.float32, device=DEV)
+    lp.lp_map_multiclass(ctx, [dev(x) for x in Ls], specs, out)
+    lp.lp_sync_status(ctx)
+    B = out.cpu().numpy()
+    ii, jj = synth.sample_pixels(H, W, 4096, 1907_02891 + 51)
+    flat = np.argpartition(B.ravel(), -64)[-64:]
+    ii = np.concatenate([ii, flat // W])
+    jj = np.concatenate([jj, flat % W])
+    ref = oracle.conv_multiclass_points_same(Ls, Ks, ii, jj)
+    assert err_maxnorm(B[ii, jj], ref) <= TOL_FP32
+    for s in specs:
+        lp.lp_spectrum_release(ctx, s)
+
+
 # --- cache, budget, validation, bounded waits ---------------------------------
 
 def test_spectrum_cache_confirms_hits_by_value(ctx):
