@@ -138,7 +138,7 @@ def plan_table() -> Dict[int, dict]:
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
                      tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
                      db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)),
-                     minbm=int(t.get("minbm", 2)), kst2=bool(t.get("kst2", True)))
+                     kst2=bool(t.get("kst2", False)))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -168,8 +168,10 @@ constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered ex
 // memory, one product + inverse per spectrum) or one single-spectrum pass per
 // spectrum (forward transform repeated)
 constexpr bool kBatch = {batch};
-// minimum resident blocks per SM of the batched column kernel
-constexpr int kMINBM = {minbm};
+// the batched column kernel parks its forward column in shared memory where
+// it fits next to the exchange buffer, else in global memory
+constexpr bool kParkG = P::SMEM_BYTES + 8 * kN > kMaxSmem;
+constexpr int kSmemM = kParkG ? kSmem : kSmem + 8 * kN;
 constexpr int kX1 = kDB1 ? 2 : 1, kX2 = kDB2 ? 2 : 1, kX3 = kDB3 ? 2 : 1;
 // one-unit-per-block column kernel: spectrum column staged in shared memory
 // (where the staging fits next to the exchange buffer)
@@ -199,8 +201,8 @@ cudaError_t set_attrs()
     if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true)>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, true, kMINBM>, kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, true, kMINBM>, kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, true, 1, false, false, kParkG>, kSmemM)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, true, 1, false, false, kParkG>, kSmemM)) != cudaSuccess) return e;
     if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p2_multiclass<P, kN, false>, kSmem)) != cudaSuccess) return e;
     if ((e = attr(p3_rows<P, kN, kF3>, kF3 * kSmem)) != cudaSuccess) return e;
@@ -238,9 +240,9 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
                      : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, dim3(a.ncols), dim3(P::T),
                                   kX2 * kSmem + kKst(false), s, a);
     }}
-    if (kBatch && a.park) {{
-        return kreal ? launch_pdl(p2_cols<P, kN, true, true, kMINBM>, dim3(a.ncols), dim3(P::T), kSmem, s, a)
-                     : launch_pdl(p2_cols<P, kN, false, true, kMINBM>, dim3(a.ncols), dim3(P::T), kSmem, s, a);
+    if (kBatch && (!kParkG || a.park)) {{
+        return kreal ? launch_pdl(p2_cols<P, kN, true, true, 1, false, false, kParkG>, dim3(a.ncols), dim3(P::T), kSmemM, s, a)
+                     : launch_pdl(p2_cols<P, kN, false, true, 1, false, false, kParkG>, dim3(a.ncols), dim3(P::T), kSmemM, s, a);
     }} else {{
         // one single-spectrum pass per spectrum (no room to park the forward
         // column, or the plan measured this faster)
@@ -355,8 +357,8 @@ def generate() -> List[str]:
                                kstage="true" if p["kstage"] else "false",
                                pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
                                db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
-                               batch=_b(p.get("batch", True)), minbm=p.get("minbm", 2),
-                               kst2=_b(p.get("kst2", True)),
+                               batch=_b(p.get("batch", True)),
+                               kst2=_b(p.get("kst2", False)),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

@@ -797,9 +797,12 @@ static void map_dims(int h, int w, int ny, int nx, int hk, int wk, lp_outmode mo
 size_t lp_park_bytes(const MapDims& d) { return 8ull * (size_t)d.ncols * (size_t)d.ny; }
 
 // the batched column pass parks its forward column spectra in the workspace
+// where they do not fit shared memory next to the exchange buffer
 static inline bool uses_park(const MapDims& d, int nchunk)
 {
-    return nchunk > 1 && d.batch && d.prec == (int)LP_PREC_FP32;
+    const SizeKernels* k = find_size(d.ny);
+    const bool global_park = k && (long long)k->smem_bytes + 8ll * d.ny > 227ll * 1024;
+    return nchunk > 1 && d.batch && global_park && d.prec == (int)LP_PREC_FP32;
 }
 
 size_t lp_workspace_bytes(const MapDims& d, int n)

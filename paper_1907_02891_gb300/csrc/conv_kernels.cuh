@@ -383,7 +383,11 @@ __device__ __forceinline__ void cp_async_wait_all();
 // memory (after the exchange buffer) with cp.async at the start, so its
 // load latency overlaps the forward transform instead of stalling the
 // product.
-template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false, bool KST = false>
+// PARKG (several spectra): the forward column is parked in global memory
+// (a.park) instead of shared memory, for lengths whose exchange buffer and
+// parked column do not fit shared memory together.
+template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false, bool KST = false,
+          bool PARKG = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2Args a)
 {
     pdl_begin();
@@ -421,11 +425,11 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     }
     Fwd::run(v, t, sm, a.twf, [&](float2(&fz)[P::EL][RL], int tt) {
         if constexpr (MULTI) {
-            // parked forward column in global memory (L2-resident while the
-            // block runs): each thread reads back only the elements it wrote,
-            // so no barrier orders the park; shared memory stays one exchange
-            // buffer, so more blocks fit an SM
-            float2* F = a.park + (size_t)c * N;
+            // parked forward column, in shared memory after the exchange
+            // buffer, or in global memory (L2-resident while the block runs);
+            // each thread reads back only the elements it wrote, so no
+            // barrier orders the park
+            float2* F = PARKG ? a.park + (size_t)c * N : smem2 + P::SMEM_ELEMS;
 #pragma unroll
             for (int e = 0; e < P::EL; ++e) {
                 const int j = tt + e * P::T;
