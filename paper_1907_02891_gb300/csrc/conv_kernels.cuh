@@ -376,6 +376,12 @@ __device__ __noinline__ void p2_spectrum_pass(const P2Args& a, int c, int s, con
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem);
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem);
+// bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16)
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit();
 __device__ __forceinline__ void cp_async_wait_all();
 
@@ -404,6 +410,12 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     const float2* col = t_column(a.T, a.ldT, c);
     constexpr int KW = KREAL ? 1 : 2;  // floats per spectrum value
     float* kst = reinterpret_cast<float*>(smem2 + (DB ? 2 : 1) * P::SMEM_ELEMS);
+    if constexpr (!MULTI && !KST) {
+        // the spectrum column is needed after the forward transform: one bulk
+        // prefetch into L2 now (no shared memory, no barrier) shortens its
+        // load latency at the product
+        if (t == 0) l2_prefetch(static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW, 16u * ((N * KW + 3) / 4));
+    }
     if constexpr (KST) {
         // ldK is a multiple of 32, so the column start is 16-byte aligned
         const float* src = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
