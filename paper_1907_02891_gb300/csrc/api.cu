@@ -882,6 +882,18 @@ static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float
     return LP_OK;
 }
 
+// Column distance of the column pass's T prefetch: about one wave of
+// resident blocks (three per SM), computed once per context.
+static int prefetch_ahead(lp_ctx* ctx)
+{
+    if (ctx->sms == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) sms = 0;
+        ctx->sms = sms > 0 ? sms : -1;
+    }
+    return ctx->sms > 0 ? 3 * ctx->sms : 0;
+}
+
 // column pass for spectra [base, base+cnt) into U (cnt blocks of ncols x ldU)
 static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectrum* const* spectra, int base,
                                 int cnt, int h, const MapDims& d, const float2* T, float2* U, float2* park,
@@ -910,6 +922,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.twf = py->fwd;
             b.twi = py->rev;
             b.park = nullptr;
+            b.ahead = 0;
             a2.tables = static_cast<const uint4*>(py->tc_tables);
             a2.err = ctx->d_err;
             a2.no_mma = (ctx->test_hook & LP_TEST_TC_NO_MMA) ? 1 : 0;
@@ -944,6 +957,7 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
         a2.twf = py->fwd;
         a2.twi = py->rev;
         a2.park = park;
+        a2.ahead = prefetch_ahead(ctx);
         const int tok = lp_pass_begin(ctx, 1, st);
         CUDA_TRY(py->k->p2(a2, kind != 0, st));
         lp_pass_end(ctx, tok, st);

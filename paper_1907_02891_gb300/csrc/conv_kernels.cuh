@@ -113,6 +113,7 @@ struct P2Args {
     int ncols;
     TwChain twf, twi;  // forward and reversed chains of the column plan
     float2* park;      // batched pass: forward column spectra, N per column
+    int ahead;         // column distance of the T prefetch into L2 (0: none)
 };
 
 struct P3Args {
@@ -415,6 +416,12 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
         // prefetch into L2 now (no shared memory, no barrier) shortens its
         // load latency at the product
         if (t == 0) l2_prefetch(static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW, 16u * ((N * KW + 3) / 4));
+        // the T columns of a block that starts about one wave of resident
+        // blocks later (a.ahead columns on), so that its first loads hit L2;
+        // the even column of each pair prefetches the pair's block
+        const int cn = c + a.ahead;
+        if (t == 32 && a.ahead > 0 && (cn & 1) == 0 && cn < a.ncols)
+            l2_prefetch(t_column(a.T, a.ldT, cn), (unsigned)(16 * a.ldT));
     }
     if constexpr (KST) {
         // ldK is a multiple of 32, so the column start is 16-byte aligned

@@ -90,6 +90,7 @@ struct lp_spectrum {
 
 struct lp_ctx {
     int device = 0;
+    int sms = 0;  // multiprocessors of the device (0: not looked up yet)
     size_t budget = 0, used = 0;
     std::mutex mem_mu, plan_mu, spec_mu, ws_mu;
     std::map<int, std::unique_ptr<PlanRec>> plans;
