@@ -858,18 +858,6 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     return LP_OK;
 }
 
-// Column distance of the column pass's T prefetch: about one wave of
-// resident blocks (three per SM), computed once per context.
-static int prefetch_ahead(lp_ctx* ctx)
-{
-    if (ctx->sms == 0) {
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) sms = 0;
-        ctx->sms = sms > 0 ? sms : -1;
-    }
-    return ctx->sms > 0 ? 3 * ctx->sms : 0;
-}
-
 // The three passes as separate launches (row pairs [pair0, pair1) for the
 // row passes), composed by lp_launch_map and by the banded host-buffer map.
 static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float* L, int h, int w, int ldl,
@@ -888,11 +876,22 @@ static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float
     a1.npairs = pair1;
     a1.ncols = d.ncols;
     a1.tw = px->fwd;
-    a1.ahead = prefetch_ahead(ctx) * 2 / 3;  // two resident row-pass blocks per SM
     const int tok = lp_pass_begin(ctx, 0, st);
     CUDA_TRY(px->k->p1(a1, st));
     lp_pass_end(ctx, tok, st);
     return LP_OK;
+}
+
+// Column distance of the column pass's T prefetch: about one wave of
+// resident blocks (three per SM), computed once per context.
+static int prefetch_ahead(lp_ctx* ctx)
+{
+    if (ctx->sms == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) sms = 0;
+        ctx->sms = sms > 0 ? sms : -1;
+    }
+    return ctx->sms > 0 ? 3 * ctx->sms : 0;
 }
 
 // column pass for spectra [base, base+cnt) into U (cnt blocks of ncols x ldU)
@@ -1293,7 +1292,6 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
         a1.npairs = npairs;
         a1.ncols = d.ncols;
         a1.tw = px->fwd;
-        a1.ahead = 0;
         CUDA_TRY(px->k->p1(a1, s));
     }
     // the real-spectrum kernel needs every class's spectrum real

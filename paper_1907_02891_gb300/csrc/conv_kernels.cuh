@@ -95,7 +95,6 @@ struct P1Args {
     int npairs;  // ceil(H/2)
     int ncols;   // Nx/2 + 1
     TwChain tw;  // forward chain of the row plan
-    int ahead;   // row-pair distance of the map-row prefetch into L2 (0: none)
 };
 
 struct P2Args {
@@ -602,14 +601,6 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
         }, P::SMEM_ELEMS);
     };
     prefetch(a.pair0 + blockIdx.x);
-    {
-        // the rows of a block that starts about one wave later, into L2
-        const int pn = a.pair0 + blockIdx.x + a.ahead;
-        const unsigned bytes = (unsigned)(a.W * 4) / 16 * 16;
-        if (threadIdx.x < 2 && a.ahead > 0 && a.vec16 && pn < a.npairs && 2 * pn + (int)threadIdx.x < a.H &&
-            bytes > 0)
-            l2_prefetch(a.L + (long long)(2 * pn + threadIdx.x) * a.ldl, bytes);
-    }
     sfor<0, UPB>([&](auto I) {
         const int pair = a.pair0 + blockIdx.x + decltype(I)::value * gridDim.x;
         if (pair < a.npairs) unit(pair);
