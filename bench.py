@@ -70,7 +70,7 @@ def parse_args():
     ap.add_argument("--forms", default="batched,split_bf16,serve",
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
-                         "serve (Poisson requests at 130%% load)")
+                         "serve (Poisson requests at 130%% and at 70%% load)")
     ap.add_argument("--forms-serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -695,7 +695,11 @@ def run_ours(args, rank, world, local_rank):
             forms["split_bf16"] = _form_map(lp, args, synth.WORKLOADS["map16384_psf801"], "split_bf16",
                                             flush, stream, dev)
         if "serve" in want:
+            # over capacity (continuous batching against back to back), and
+            # at 70 % load (latency beside throughput)
             forms["serve"] = serve_measure(args.forms_serve_requests, 1.3, args.slots, local_rank)
+            forms["serve_load70"] = serve_measure(args.forms_serve_requests, 0.7, args.slots, local_rank,
+                                                  check=False)
     if rank != 0:
         return
     line = {
