@@ -138,7 +138,7 @@ def plan_table() -> Dict[int, dict]:
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
                      tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
                      db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)),
-                     kst2=bool(t.get("kst2", False)))
+                     kst2=bool(t.get("kst2", False)), packed=bool(t.get("packed", False)))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -146,6 +146,8 @@ def plan_table() -> Dict[int, dict]:
 
 
 _SIZE_TU = """// generated by paper_1907_02891_gb300/build.py -- one supported FFT length
+// packed FP32x2 complex arithmetic in this length's DFTs
+#define LP_PACKED_FP32 {packed}
 #include "conv_kernels.cuh"
 #include "lp_internal.h"
 #include "tc_kernels.cuh"
@@ -358,7 +360,7 @@ def generate() -> List[str]:
                                pf1=_b(p["pf"][0]), pf2=_b(p["pf"][1]), pf3=_b(p["pf"][2]),
                                db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
                                batch=_b(p.get("batch", True)),
-                               kst2=_b(p.get("kst2", False)),
+                               kst2=_b(p.get("kst2", False)), packed=int(bool(p.get("packed", False))),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(GEN, f"size_{n}.cu")
         _write_if_changed(path, text)

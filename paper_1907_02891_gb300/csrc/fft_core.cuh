@@ -128,6 +128,14 @@ template <class C> __device__ __forceinline__ C cfma(C a, typename Scalar<C>::ty
 // FP32 complex values {re, im} are a natural pair for the packed FP32x2
 // instructions: an addition, a subtraction, a real scaling or a real
 // multiply-add of a complex value is one add / sub / mul / fma .f32x2.
+// A plan chooses per length (LP_PACKED_FP32, set by the length's translation
+// unit, whose device code is compiled on its own): the packed constants take
+// registers, which costs more than it saves in the register-bound kernels of
+// some lengths.
+#ifndef LP_PACKED_FP32
+#define LP_PACKED_FP32 1
+#endif
+#if LP_PACKED_FP32
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b)
 {
@@ -141,6 +149,7 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b)
 }
 __device__ __forceinline__ float2 cscale(float2 a, float c) { return __fmul2_rn(a, make_float2(c, c)); }
 __device__ __forceinline__ float2 cfma(float2 a, float c, float2 acc) { return __ffma2_rn(a, make_float2(c, c), acc); }
+#endif
 template <class C> __device__ __forceinline__ C cmul(C a, C b)
 {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);

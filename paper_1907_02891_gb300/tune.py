@@ -94,7 +94,7 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
                              pf1=B._b(plan["pf"][0]), pf2=B._b(plan["pf"][1]), pf3=B._b(plan["pf"][2]),
                              db1=B._b(plan["db"][0]), db2=B._b(plan["db"][1]), db3=B._b(plan["db"][2]),
                              batch=B._b(plan.get("batch", True)),
-                             kst2=B._b(plan.get("kst2", False)),
+                             kst2=B._b(plan.get("kst2", False)), packed=int(bool(plan.get("packed", False))),
                              rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
     src = os.path.join(d, f"size_{n}.cu")
     with open(src, "w") as fh:
