@@ -276,6 +276,21 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
                 db[i], minb[i] = 1, p["minb"][0]
     out.update(db=db, minb=minb, tuned_total_us=sum(best_pass.values()) * 1e3)
     log(f"N={n}: refined db={db} minb={minb} (sum {out['tuned_total_us']:.1f} us)")
+    # packed FP32x2 DFT arithmetic: one switch for the whole length (its
+    # constants take registers, which can make a register-capped kernel
+    # spill); kept where all three passes together are faster
+    p = dict(out, packed=not out.get("packed", False))
+    lib = build_or_error(p)
+    if isinstance(lib, str):
+        try:
+            t = time_variant(lib, n, 200 if n <= 5200 else 40, side, psf, nspec)
+            log(f"  packed={int(p['packed'])}: " + " ".join(f"{k}={v * 1e3:.1f}us" for k, v in t.items()))
+            if sum(t.values()) < sum(best_pass.values()) * 0.99:
+                best_pass = dict(t)
+                out.update(packed=p["packed"], tuned_total_us=sum(best_pass.values()) * 1e3)
+        except Exception as e:
+            log(f"  skip packed={int(p['packed'])}: {str(e).splitlines()[-1][:120]}")
+    log(f"N={n}: packed={out.get('packed', False)}")
     if nspec > 1:
         # several spectra: the batched column kernel against one single-
         # spectrum pass per spectrum
