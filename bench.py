@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--load", type=float, default=0.7,
                     help="offered load as a fraction of the measured back-to-back capacity")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-log", default=None,
+                    help="--mode serve: append one JSON line per request to this file")
     ap.add_argument("--forms", default="batched,split_bf16,serve",
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
@@ -118,7 +120,7 @@ def kernel_source_sha(extra=(), lengths=()):
                 if t and not t.startswith(("//", "#", "/*", "*")):
                     h.update(t.encode())
     try:
-        with open(os.path.join(ROOT, TUNED_PLANS)) as fh:
+        with open(os.environ.get("LP_TUNE_CACHE") or os.path.join(ROOT, TUNED_PLANS)) as fh:
             tuned = json.load(fh)
     except (OSError, ValueError):
         tuned = {}
@@ -731,13 +733,15 @@ def run_ours(args, rank, world, local_rank):
 # serving run
 # ----------------------------------------------------------------------------
 
-def serve_measure(n_requests, load, slots, local_rank, check=True):
+def serve_measure(n_requests, load, slots, local_rank, check=True, log_path=None):
     """Poisson arrivals of map requests (tile side uniform on 256..8192, 1-8
     PSFs of a bank of 8 cached 201^2 spectra) through the request scheduler;
     p50/p99 latency and Mpix/s.  The same requests run back to back through
     lp_map on one stream give the queue-alone reference.  With `check`, the
     last requests' outputs are compared bitwise with the same requests run
-    alone, and the last one against the oracle (CPU-baseline leg)."""
+    alone, and the last one against the oracle (CPU-baseline leg).  With
+    `log_path`, the scheduler appends one JSON line per timed request there
+    (lp_serve_log)."""
     import threading
     import numpy as np
     import torch
@@ -788,6 +792,8 @@ def serve_measure(n_requests, load, slots, local_rank, check=True):
     warm = [lp.lp_serve_submit(ctx, *call_args(big, k)) for k in range(slots)]
     for t in warm:
         lp.lp_serve_poll(ctx, t)
+    if log_path:
+        lp.lp_serve_log(ctx, log_path)
     tickets = [None] * len(reqs)
     lat = [None] * len(reqs)
     done_t = [0.0] * len(reqs)
@@ -861,7 +867,8 @@ def serve_measure(n_requests, load, slots, local_rank, check=True):
 def run_serve(args, rank, world, local_rank):
     if rank != 0:
         return
-    print(json.dumps(serve_measure(args.requests, args.load, args.slots, local_rank)), flush=True)
+    print(json.dumps(serve_measure(args.requests, args.load, args.slots, local_rank, log_path=args.serve_log)),
+          flush=True)
 
 
 def main():

@@ -303,6 +303,21 @@ lp_status lp_serve_stats(lp_ctx* ctx, uint64_t* completed, uint64_t* failed, int
 lp_status lp_serve_stop(lp_ctx* ctx);
 
 /*
+ * Per-request log of the serving loop (metrics; no counterpart in the
+ * paper).  While a log file is set, every finished request appends one JSON
+ * line: ticket, status, h, w, n_psf, mode, precision, workspace_bytes,
+ * output_mpix (h w n_psf / 1e6) and the host-clock times submit_ms,
+ * start_ms (admitted and launched), end_ms (completion seen by the
+ * scheduler's event poll, which runs every 20 us while requests are in
+ * flight), all in ms from lp_serve_start, plus queue_ms = start - submit and
+ * latency_ms = end - submit (the value lp_serve_poll returns).  path is
+ * opened for appending (LP_ERR_INVALID if it cannot be); NULL or "" closes
+ * the log.  lp_serve_stop closes it too.  LP_ERR_BUSY when serving has not
+ * started.
+ */
+lp_status lp_serve_log(lp_ctx* ctx, const char* path);
+
+/*
  * Pass timing (tracing).  While enabled, every map call records CUDA events
  * around each of its kernel passes on its own stream:
  *   pass 0 = row forward transform (P1), 1 = column transform with the

@@ -97,6 +97,13 @@ def choose_plan(n: int) -> Tuple[int, ...]:
 TUNED_JSON = os.path.join(HERE, "tuned_plans.json")
 
 
+def tuned_json_path() -> str:
+    """The measured plans: the file named by $LP_TUNE_CACHE when set (same
+    form, e.g. plans re-measured on another GPU), else tuned_plans.json
+    beside this file."""
+    return os.environ.get("LP_TUNE_CACHE") or TUNED_JSON
+
+
 def plan_table_entry(n: int) -> dict:
     """Heuristic plan of one length (used when the autotuner has not
     measured it)."""
@@ -126,8 +133,9 @@ def plan_table() -> Dict[int, dict]:
     """Plan of every supported length: the autotuner's measured choice from
     tuned_plans.json where there is one, the heuristic otherwise."""
     tuned = {}
-    if os.path.exists(TUNED_JSON):
-        with open(TUNED_JSON) as fh:
+    path = tuned_json_path()
+    if os.path.exists(path):
+        with open(path) as fh:
             tuned = json.load(fh)
     table = {}
     for n in SIZES:

@@ -7,11 +7,13 @@
 // a CUDA stream and a workspace, so requests admitted while others are on the
 // GPU run concurrently with them.  Completion is observed with CUDA events;
 // latency = completion - submission (host clock).  Spectra and plans are
-// the context's device-resident caches, shared by all requests.
+// the context's device-resident caches, shared by all requests.  With a log
+// file set (lp_serve_log), every finished request appends one JSON line.
 #include <cuda_runtime.h>
 
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -46,6 +48,7 @@ struct Slot {
     size_t footprint = 0;
     std::vector<const lp_spectrum*> spectra;  // references held by the running request
     Clock::time_point submitted, started;
+    int h = 0, w = 0, n = 0, mode = 0, prec = 0;  // for the request log
 };
 
 struct Result {
@@ -72,7 +75,15 @@ struct ServeState {
     size_t max_queue = 1 << 16;
     // counters
     uint64_t n_done = 0, n_failed = 0;
+    // per-request log (JSON lines), times in ms from t0
+    FILE* log = nullptr;
+    Clock::time_point t0 = Clock::now();
 };
+
+static double ms_since(Clock::time_point t0, Clock::time_point t)
+{
+    return std::chrono::duration<double, std::milli>(t - t0).count();
+}
 
 
 
@@ -86,6 +97,16 @@ static void finish_slot(ServeState* S, Slot& sl, lp_status st)
     r.latency_ms = std::chrono::duration<double, std::milli>(now - sl.submitted).count();
     r.queue_ms = std::chrono::duration<double, std::milli>(sl.started - sl.submitted).count();
     S->done[sl.ticket] = r;
+    if (S->log) {
+        // completion is seen by the scheduler's event poll (every 20 us while requests run)
+        std::fprintf(S->log,
+                     "{\"ticket\": %llu, \"status\": %d, \"h\": %d, \"w\": %d, \"n_psf\": %d, \"mode\": %d, "
+                     "\"precision\": %d, \"workspace_bytes\": %zu, \"output_mpix\": %.6f, \"submit_ms\": %.4f, "
+                     "\"start_ms\": %.4f, \"end_ms\": %.4f, \"queue_ms\": %.4f, \"latency_ms\": %.4f}\n",
+                     (unsigned long long)sl.ticket, (int)st, sl.h, sl.w, sl.n, sl.mode, sl.prec, sl.footprint,
+                     (double)sl.h * sl.w * sl.n / 1e6, ms_since(S->t0, sl.submitted), ms_since(S->t0, sl.started),
+                     ms_since(S->t0, now), r.queue_ms, r.latency_ms);
+    }
     S->reserved -= sl.footprint;
     sl.busy = false;
     sl.footprint = 0;
@@ -135,6 +156,11 @@ static void scheduler_loop(ServeState* S)
             sl.submitted = rq.submitted;
             sl.started = Clock::now();
             sl.footprint = rq.footprint;
+            sl.h = rq.h;
+            sl.w = rq.w;
+            sl.n = (int)rq.spectra.size();
+            sl.mode = (int)rq.mode;
+            sl.prec = (int)rq.spectra[0]->prec;
             sl.busy = true;
             S->reserved += rq.footprint;
             if (st == LP_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = LP_ERR_CUDA;
@@ -272,6 +298,26 @@ extern "C" lp_status lp_serve_stats(lp_ctx* ctx, uint64_t* completed, uint64_t* 
     return LP_OK;
 }
 
+extern "C" lp_status lp_serve_log(lp_ctx* ctx, const char* path)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_serve_log: NULL context");
+    ServeState* S = ctx->serve;
+    if (!S) return lp_fail(LP_ERR_BUSY, "lp_serve_log: serving not started");
+    FILE* f = nullptr;
+    if (path && path[0]) {
+        f = std::fopen(path, "a");
+        if (!f) return lp_fail(LP_ERR_INVALID, "lp_serve_log: cannot open %s for appending", path);
+    }
+    FILE* old;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        old = S->log;
+        S->log = f;
+    }
+    if (old) std::fclose(old);
+    return LP_OK;
+}
+
 extern "C" lp_status lp_serve_stop(lp_ctx* ctx)
 {
     if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_serve_stop: NULL context");
@@ -301,6 +347,7 @@ extern "C" lp_status lp_serve_stop(lp_ctx* ctx)
         cudaEventDestroy(sl.done);
         cudaStreamDestroy(sl.stream);
     }
+    if (S->log) std::fclose(S->log);
     ctx->serve = nullptr;
     delete S;
     if (prev >= 0) cudaSetDevice(prev);

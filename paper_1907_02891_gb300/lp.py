@@ -36,6 +36,7 @@ EXPORTS = (
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
     "lp_set_test_hook",
     "lp_serve_start", "lp_serve_submit", "lp_serve_poll", "lp_serve_stats", "lp_serve_stop",
+    "lp_serve_log",
 )
 
 
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_serve_stats": ([_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                             ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
         "lp_serve_stop": ([_vp], _i),
+        "lp_serve_log": ([_vp, ctypes.c_char_p], _i),
         "lp_get_pass_timing": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
@@ -343,6 +345,11 @@ def lp_serve_stats(ctx: int) -> dict:
     _check(load_library().lp_serve_stats(ctx, ctypes.byref(c), ctypes.byref(f), ctypes.byref(q),
                                          ctypes.byref(r)), "lp_serve_stats")
     return dict(completed=c.value, failed=f.value, queued=q.value, running=r.value)
+
+
+def lp_serve_log(ctx: int, path) -> None:
+    """Append one JSON line per finished request to path (None: stop logging)."""
+    _check(load_library().lp_serve_log(ctx, None if path is None else str(path).encode()), "lp_serve_log")
 
 
 def lp_serve_stop(ctx: int) -> None:

@@ -8,7 +8,8 @@ size is N x N on the GPU, and keeps, for the fastest radix sequence, the best
 knob setting of each pass, then refines it (double-buffered exchange; with
 several spectra per map, one single-spectrum column pass per spectrum
 against the batched kernel).  The result is written to ``tuned_plans.json``
-beside this file; ``build.py`` uses it for every length it lists.
+beside this file (or to the file $LP_TUNE_CACHE names); ``build.py`` uses
+it for every length it lists.
 
     python -m paper_1907_02891_gb300.tune --sizes 4704 [--quick] \
         [--map-side 4096 --psf 541 --nspec 1] [--plan 21,16,14 ...]
@@ -37,7 +38,6 @@ from typing import Dict, List, Tuple
 from . import build as B
 
 TUNE_DIR = os.path.join(B.OUT, "tune")
-TUNED_JSON = os.path.join(B.HERE, "tuned_plans.json")
 COMMON_SRCS = ("api.cu", "spectrum.cu", "noalloc.cu", "serve.cpp")
 
 
@@ -314,7 +314,8 @@ def main() -> None:
     ap.add_argument("--sizes", type=int, nargs="+", required=True)
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--jobs", type=int, default=0)
-    ap.add_argument("--out", default=TUNED_JSON)
+    ap.add_argument("--out", default=B.tuned_json_path(),
+                    help="plan file to update (default: $LP_TUNE_CACHE, else tuned_plans.json)")
     ap.add_argument("--log", default=None)
     ap.add_argument("--plan", action="append", default=[],
                     help="radix sequence to try, e.g. 7,7,8,12 (repeatable; default: the candidate list)")

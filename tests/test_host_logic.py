@@ -77,6 +77,29 @@ def test_fingerprint_ignores_notes_but_not_knobs(tmp_path, monkeypatch):
     assert bench.kernel_source_sha(lengths=(4704,)) != base
 
 
+def test_tune_cache_env_names_the_plan_file(tmp_path, monkeypatch):
+    """$LP_TUNE_CACHE replaces tuned_plans.json for the build's plan table,
+    the tuner's default output and the bench's kernel fingerprint."""
+    with open(B.TUNED_JSON) as fh:
+        tuned = json.load(fh)
+    base_plan = B.plan_table()[4704]
+    base_sha = bench.kernel_source_sha(lengths=(4704,))
+    alt = dict(tuned)
+    alt["4704"] = dict(tuned["4704"], radices=[14, 16, 21], minb=[1, 1, 1])
+    p = tmp_path / "plans.json"
+    p.write_text(json.dumps(alt))
+    monkeypatch.setenv("LP_TUNE_CACHE", str(p))
+    assert B.tuned_json_path() == str(p)
+    got = B.plan_table()[4704]
+    assert got["radices"] == [14, 16, 21] and got["minb"] == [1, 1, 1]
+    assert got["threads"] == B.threads_for(4704, [14, 16, 21])
+    assert bench.kernel_source_sha(lengths=(4704,)) != base_sha
+    monkeypatch.delenv("LP_TUNE_CACHE")
+    assert B.tuned_json_path() == B.TUNED_JSON
+    assert B.plan_table()[4704] == base_plan
+    assert bench.kernel_source_sha(lengths=(4704,)) == base_sha
+
+
 def test_host_fft_comparator_computes_eq7():
     pytest.importorskip("scipy")
     oracle.build()

@@ -208,3 +208,42 @@ def test_release_mid_run_does_not_stall_the_slots():
                 assert torch.equal(x, y)
     finally:
         lp.lp_destroy(ctx)
+
+
+def test_request_log_lines(tmp_path):
+    """The per-request JSON-lines log: one line per finished request, with
+    its sizes and host-clock times in order (submit <= start <= end) and the
+    latency lp_serve_poll returned."""
+    import json
+    sides = (64, 256)
+    ctx = lp.lp_create(0)
+    try:
+        _, spectra = _bank(ctx, sides)
+        reqs = _requests(12, sides, 5)
+        lp.lp_serve_start(ctx, 2)
+        with pytest.raises(lp.LpError):
+            lp.lp_serve_log(ctx, str(tmp_path / "no_such_dir" / "x.jsonl"))
+        path = tmp_path / "serve.jsonl"
+        lp.lp_serve_log(ctx, path)
+        outs, tickets = [], []
+        for s, ks, L in reqs:
+            o = [torch.empty((s, s), device=DEV) for _ in ks]
+            tickets.append(lp.lp_serve_submit(ctx, L, [spectra[(s, i)] for i in ks], o))
+            outs.append(o)
+        lats = {t: lp.lp_serve_poll(ctx, t, timeout_ms=60000) for t in tickets}
+        lp.lp_serve_stop(ctx)   # closes the log
+        lines = [json.loads(x) for x in path.read_text().splitlines()]
+        assert sorted(r["ticket"] for r in lines) == sorted(tickets)
+        by = {r["ticket"]: r for r in lines}
+        for t, (s, ks, _) in zip(tickets, reqs):
+            r = by[t]
+            assert r["status"] == 0 and r["h"] == s and r["w"] == s and r["n_psf"] == len(ks)
+            assert r["mode"] == lp.LP_OUT_SAME and r["precision"] == lp.LP_PREC_FP32
+            assert r["workspace_bytes"] > 0
+            assert abs(r["output_mpix"] - s * s * len(ks) / 1e6) < 1e-6
+            assert 0 <= r["submit_ms"] <= r["start_ms"] <= r["end_ms"]
+            assert abs(r["latency_ms"] - (r["end_ms"] - r["submit_ms"])) < 1e-2
+            assert abs(r["queue_ms"] - (r["start_ms"] - r["submit_ms"])) < 1e-2
+            assert abs(r["latency_ms"] - lats[t]) < 1e-3
+    finally:
+        lp.lp_destroy(ctx)
