@@ -36,9 +36,10 @@ UNIT = "Mpix/s"
 DEFAULT_WORKLOAD = "map4096_psf541"
 FALLBACK_HBM_GBS = 6800.0
 PASSES = ("p1_rows", "p2_cols", "p3_rows")
+# the kernel headers; build.py contributes its generated-source templates
+# and compiler flags (the rest of it is the compile driver)
 KERNEL_SOURCES = ("paper_1907_02891_gb300/csrc/fft_core.cuh",
-                  "paper_1907_02891_gb300/csrc/conv_kernels.cuh",
-                  "paper_1907_02891_gb300/build.py")
+                  "paper_1907_02891_gb300/csrc/conv_kernels.cuh")
 TUNED_PLANS = "paper_1907_02891_gb300/tuned_plans.json"
 TC_SOURCES = ("paper_1907_02891_gb300/csrc/tc_kernels.cuh",)
 
@@ -69,9 +70,10 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-log", default=None,
                     help="--mode serve: append one JSON line per request to this file")
-    ap.add_argument("--forms", default="batched,split_bf16,serve",
+    ap.add_argument("--forms", default="batched,split_bf16,tiled,serve",
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
+                         "tiled (17800 x 21000, 801^2 PSF, overlap-save tiles), "
                          "serve (Poisson requests at 130%% and at 70%% load)")
     ap.add_argument("--forms-serve-requests", type=int, default=400)
     return ap.parse_args()
@@ -112,13 +114,16 @@ def whole_job_mpix_s(px_per_rank_per_step: float, steps: int, world: int, max_ms
 def kernel_source_sha(extra=(), lengths=()):
     """Fingerprint of the kernel sources and of the measured plans of the
     given FFT lengths (the plans of other lengths do not change them)."""
+    from paper_1907_02891_gb300 import build as B
     h = hashlib.sha1()
     for p in KERNEL_SOURCES + tuple(extra):
         with open(os.path.join(ROOT, p), encoding="utf-8") as fh:
             for line in fh:  # whole-line comments and blank lines change no kernel
                 t = line.strip()
-                if t and not t.startswith(("//", "#", "/*", "*")):
+                if t and not t.startswith(("//", "/*", "*")):
                     h.update(t.encode())
+    for part in (B._SIZE_TU, B._REGISTRY_TU, " ".join(B.ARCH), " ".join(B.NVCC_FLAGS)):
+        h.update(part.encode())
     try:
         with open(os.environ.get("LP_TUNE_CACHE") or os.path.join(ROOT, TUNED_PLANS)) as fh:
             tuned = json.load(fh)
@@ -551,6 +556,71 @@ def _form_map(lp, args, wl, prec_name, flush, stream, dev, compare_fp32=True, pe
         lp.lp_destroy(ctx)
 
 
+def _form_tiled(lp, args, wl, flush, stream, dev):
+    """The tiled form: a map longer than the longest FFT length, in
+    overlap-save tiles (lp_map_tiled) at the padded size lp_tiled_pad picks;
+    Mpix/s, the error against the oracle, and the plain FP32 path beside it
+    on the largest square sub-map one transform of the longest length
+    holds."""
+    import torch
+    H, W = wl.H, wl.W
+    L_host = wl.radiance()
+    (K,) = wl.psfs()
+    hk = K.shape[0]
+    n_max = max(lp.supported_sizes())
+    ctx = lp.lp_create(dev.index or 0)
+    try:
+        L = torch.from_numpy(L_host).to(dev)
+        Kd = torch.from_numpy(K).to(dev)
+        ny, nx = lp.lp_tiled_pad(H, W, hk, hk)
+        spec = lp.lp_kernel_spectrum(ctx, Kd, pad_ny=ny, pad_nx=nx)
+        out = torch.empty((H, W), dtype=torch.float32, device=dev)
+        steps, warm = max(3, min(args.steps, 10)), max(3, min(args.warmup, 5))
+
+        def one():
+            lp.lp_map_tiled(ctx, L, [spec], [out])
+
+        for _ in range(warm):
+            flush.zero_()
+            one()
+        lp.lp_sync_status(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            one()
+            b.record(stream)
+        torch.cuda.synchronize()
+        lp.lp_sync_status(ctx)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        th, tw = ny - (hk - 1), nx - (hk - 1)
+        tiles = -(-H // th) * -(-W // tw)
+        err = cpu_baseline_leg_error(L_host, [K], [out], wl.seed + 300)
+        lp.lp_spectrum_release(ctx, spec)
+        rec = {"workload": wl.name, "map": f"{H}x{W}", "psf": f"{hk}x{hk}", "n_psf": 1,
+               "padded": f"{ny}x{nx}", "tiles": tiles, "tile_output": f"{th}x{tw}", "precision": "fp32",
+               "mpix_s": H * W / (ms / 1e3) / 1e6, "ms_per_step": ms, "steps": steps,
+               "max_norm_err": err, "tolerance": 1e-5}
+        # the plain path on the largest sub-map one transform of the longest
+        # length holds
+        spec = lp.lp_kernel_spectrum(ctx, Kd, pad_ny=n_max, pad_nx=n_max)
+        side = n_max - (hk - 1)
+        sub = L[:side, :side]
+        osub = out[:side, :side]
+        pms = statistics.mean(_time_maps(lp, ctx, sub, [spec], [osub], lp.LP_PREC_FP32, steps, warm, flush,
+                                         stream))
+        rec["plain_fp32"] = {"map": f"{side}x{side}", "mpix_s": side * side / (pms / 1e3) / 1e6,
+                             "ms_per_step": pms, "padded": f"{n_max}x{n_max}",
+                             "what": "lp_map on the largest square sub-map one transform holds"}
+        rec["speedup_vs_plain_fp32"] = rec["mpix_s"] / rec["plain_fp32"]["mpix_s"]
+        lp.lp_spectrum_release(ctx, spec)
+        lp.lp_sync_status(ctx)
+        return rec
+    finally:
+        lp.lp_destroy(ctx)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -696,6 +766,8 @@ def run_ours(args, rank, world, local_rank):
         if "split_bf16" in want:
             forms["split_bf16"] = _form_map(lp, args, synth.WORKLOADS["map16384_psf801"], "split_bf16",
                                             flush, stream, dev)
+        if "tiled" in want:
+            forms["tiled"] = _form_tiled(lp, args, synth.WORKLOADS["map17800x21000_psf801"], flush, stream, dev)
         if "serve" in want:
             # over capacity (continuous batching against back to back), and
             # at 70 % load (latency beside throughput)

@@ -272,6 +272,37 @@ lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
 lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
 
 /*
+ * Maps larger than the padded size (overlap-save tiling; Sec. 4 computes
+ * extended regions band by band, here the pieces share one grid).  The SAME-mode result of
+ * lp_map for an h x w map of any size, computed in tiles of
+ * (Ny - hk + 1) x (Nx - wk + 1) output pixels: each tile convolves the input
+ * window that covers it plus the PSF's reach ((hk - 1) / 2 rows,
+ * (wk - 1) / 2 columns, clipped to the map) in one P1 / P2 / P3 sequence,
+ * which is exact for the tile's pixels (no wrap-around reaches them), and
+ * writes its part of out[] in place.  The spectra need one PSF size and
+ * any padded size Ny > hk - 1, Nx > wk - 1 (build them with an explicit
+ * pad_ny / pad_nx; a larger pad gives fewer, larger tiles).  L, out[],
+ * ldl, ldo, prec and stream as lp_map; the workspace holds one tile, and the
+ * tiles run in stream order.  Errors as lp_map; LP_ERR_INVALID also for
+ * spectra of different PSF sizes or a pad that leaves no tile.
+ */
+lp_status lp_map_tiled(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                       const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                       lp_precision prec, void* stream);
+
+/*
+ * Padded size for lp_map_tiled (host only, no device needed): per dimension
+ * the supported length N >= hk (>= wk) that minimises the points transformed
+ * over all tiles, ceil(h / (N - hk + 1)) * N (ties: fewer tiles); for
+ * LP_PREC_SPLIT_BF16 the column length has the tensor-core pass.  A map
+ * that one transform holds whole usually gets the lp_map padding (one tile).
+ * Errors: LP_ERR_INVALID (empty map, even or non-positive PSF sides, NULL
+ * outputs), LP_ERR_UNSUPPORTED (precision, or no length holds the PSF);
+ * the outputs are -1 on error.
+ */
+lp_status lp_tiled_pad(int h, int w, int hk, int wk, lp_precision prec, int* pad_ny, int* pad_nx);
+
+/*
  * Serving: continuous batching of map requests.  lp_serve_start creates
  * n_slots CUDA streams (each with its own workspace) and a scheduler thread.
  * lp_serve_submit validates a request exactly like lp_map (LP_OUT_* mode;

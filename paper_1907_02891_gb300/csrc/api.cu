@@ -15,6 +15,7 @@
 #include <string>
 #include <thread>
 #include <tuple>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/lp.h"
@@ -90,6 +91,45 @@ static int tc_supported_size(int n)
         if (N >= n && kAllSizes[i]->tc_smem > 0 && (best < 0 || N < best)) best = N;
     }
     return best;
+}
+
+// Padded length of one dimension for the tiled map: the supported length
+// N >= k that minimises the transformed points of that dimension,
+// ceil(n / (N - k + 1)) * N (ties: fewer tiles); with tc, only lengths that
+// have the tensor-core column pass.
+static int tile_length(int n, int k, bool tc)
+{
+    long long best_cost = -1;
+    int best = -1, best_tiles = 0;
+    for (int i = 0; i < kNumSizes; ++i) {
+        const int N = kAllSizes[i]->N;
+        if (N < k || (tc && kAllSizes[i]->tc_smem == 0)) continue;
+        const int t = N - k + 1;
+        const int tiles = (n + t - 1) / t;
+        const long long cost = (long long)tiles * N;
+        if (best < 0 || cost < best_cost || (cost == best_cost && tiles < best_tiles)) {
+            best = N;
+            best_cost = cost;
+            best_tiles = tiles;
+        }
+    }
+    return best;
+}
+
+extern "C" lp_status lp_tiled_pad(int h, int w, int hk, int wk, lp_precision prec, int* pad_ny, int* pad_nx)
+{
+    if (!pad_ny || !pad_nx) return lp_fail(LP_ERR_INVALID, "lp_tiled_pad: NULL argument");
+    *pad_ny = *pad_nx = -1;
+    if (h < 1 || w < 1) return lp_fail(LP_ERR_INVALID, "lp_tiled_pad: empty map %d x %d", h, w);
+    if (hk < 1 || wk < 1 || hk % 2 == 0 || wk % 2 == 0)
+        return lp_fail(LP_ERR_INVALID, "lp_tiled_pad: PSF sides must be odd and >= 1 (got %d x %d)", hk, wk);
+    if (prec != LP_PREC_FP32 && prec != LP_PREC_SPLIT_BF16)
+        return lp_fail(LP_ERR_UNSUPPORTED, "lp_tiled_pad: precision %d is not built", (int)prec);
+    const int ny = tile_length(h, hk, prec == LP_PREC_SPLIT_BF16), nx = tile_length(w, wk, false);
+    if (ny < 0 || nx < 0) return lp_fail(LP_ERR_UNSUPPORTED, "lp_tiled_pad: no supported length holds the PSF");
+    *pad_ny = ny;
+    *pad_nx = nx;
+    return LP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -821,9 +861,12 @@ extern "C" size_t lp_map_workspace_bytes(int h, int w, int ny, int nx, int hk, i
     return lp_workspace_bytes(d, n);
 }
 
-lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
-                          const lp_spectrum* const* spectra, int n, const void* out, int ldo,
-                          lp_outmode mode, lp_precision prec, MapDims* d)
+// Checks shared by every map entry point.  need_pad: the spectra's padded
+// size must hold the whole linear convolution of the map (Sec. 2.5); the
+// tiled map instead needs spectra of one PSF size (its tile geometry).
+static lp_status validate_map_args(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                                   const lp_spectrum* const* spectra, int n, const void* out, lp_outmode mode,
+                                   lp_precision prec, bool need_pad)
 {
     if (!ctx || !L || !spectra || !out) return lp_fail(LP_ERR_INVALID, "lp_map: NULL argument");
     if (h < 1 || w < 1) return lp_fail(LP_ERR_INVALID, "lp_map: empty map %d x %d", h, w);
@@ -841,7 +884,9 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         if (s->ny != s0->ny || s->nx != s0->nx)
             return lp_fail(LP_ERR_INVALID, "lp_map: spectra differ in padded size (%dx%d vs %dx%d)", s->ny,
                            s->nx, s0->ny, s0->nx);
-        if (s->ny < h + s->hk - 1 || s->nx < w + s->wk - 1)
+        if (!need_pad && (s->hk != s0->hk || s->wk != s0->wk))
+            return lp_fail(LP_ERR_INVALID, "lp_map_tiled: spectra of different PSF sizes");
+        if (need_pad && (s->ny < h + s->hk - 1 || s->nx < w + s->wk - 1))
             return lp_fail(LP_ERR_INVALID,
                            "lp_map: spectrum %d padded to %d x %d, the map %d x %d with a %d x %d PSF "
                            "needs >= %d x %d",
@@ -852,6 +897,16 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     }
     if (prec == LP_PREC_SPLIT_BF16 && find_size(s0->ny)->tc_smem == 0)
         return lp_fail(LP_ERR_UNSUPPORTED, "lp_map: column length %d has no split-precision pass", s0->ny);
+    return LP_OK;
+}
+
+lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                          const lp_spectrum* const* spectra, int n, const void* out, int ldo,
+                          lp_outmode mode, lp_precision prec, MapDims* d)
+{
+    const lp_status st = validate_map_args(ctx, L, h, w, ldl, spectra, n, out, mode, prec, true);
+    if (st != LP_OK) return st;
+    const lp_spectrum* s0 = spectra[0];
     map_dims(h, w, s0->ny, s0->nx, s0->hk, s0->wk, mode, d);
     d->prec = (int)prec;
     if (ldo < d->Wout) return lp_fail(LP_ERR_INVALID, "lp_map: ldo %d < output width %d", ldo, d->Wout);
@@ -1047,6 +1102,77 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
     return lp_launch_map(ctx, L, h, w, ldl, spectra, n, out, ldo, d, ws, s);
+}
+
+// Maps larger than the spectra's padded size: overlap-save tiles.  Sec. 4
+// computes extended regions band by band; here the pieces share one grid,
+// and each carries the PSF's reach around it as margin so that its pixels
+// see every source within the PSF.  Output tile rows [a, a + th) of the SAME
+// result need the input rows [a - cy, a + th + cy) (cy = (hk - 1) / 2),
+// clipped to the map (rows outside it are zero).  In the Ny-point circular
+// convolution of that window the tile's rows receive no wrapped-around term
+// when Ny >= th + 2 cy: the tile starts r0 <= cy rows into the window and
+// the window ends at most th + cy rows after the tile's start, so a kept
+// output row o and an input row i of the window satisfy |o - i| <= th + cy
+// - 1, and o - i +- Ny never falls within the PSF's support [-cy, cy].
+// Hence th = Ny - (hk - 1) (hk = 2 cy + 1), and tw = Nx - (wk - 1) alike.  Each tile is one P1 / P2 / P3 sequence on the
+// window (row and column offsets of the crop r0 = a - window start,
+// c0 alike), writing its tile of out[] in place; tiles run in stream order
+// and share one workspace.
+extern "C" lp_status lp_map_tiled(lp_ctx* ctx, const float* L, int h, int w, int ldl,
+                                  const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
+                                  lp_precision prec, void* stream)
+{
+    lp_status st = validate_map_args(ctx, L, h, w, ldl, spectra, n, out, LP_OUT_SAME, prec, false);
+    if (st != LP_OK) return st;
+    if (ldo < w) return lp_fail(LP_ERR_INVALID, "lp_map_tiled: ldo %d < output width %d", ldo, w);
+    const lp_spectrum* s0 = spectra[0];
+    const int ny = s0->ny, nx = s0->nx, hk = s0->hk, wk = s0->wk;
+    const int cy = (hk - 1) / 2, cx = (wk - 1) / 2;
+    const int th = ny - (hk - 1), tw = nx - (wk - 1);
+    if (th < 1 || tw < 1)
+        return lp_fail(LP_ERR_INVALID, "lp_map_tiled: padded size %d x %d leaves no tile for a %d x %d PSF", ny, nx,
+                       hk, wk);
+    for (int k = 0; k < n; ++k) {
+        if (!out[k]) return lp_fail(LP_ERR_INVALID, "lp_map_tiled: out[%d] is NULL", k);
+        const char* o0 = reinterpret_cast<const char*>(out[k]);
+        const char* o1 = o0 + 4ull * ((size_t)(h - 1) * ldo + w);
+        const char* l0 = reinterpret_cast<const char*>(L);
+        const char* l1 = l0 + 4ull * ((size_t)(h - 1) * ldl + w);
+        if (o0 < l1 && l0 < o1) return lp_fail(LP_ERR_INVALID, "lp_map_tiled: out[%d] overlaps L", k);
+    }
+    DeviceGuard dg(ctx->device);
+    lp_reap_released(ctx, false);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // one workspace for the largest tile: window min(h, th + 2 cy) x
+    // min(w, tw + 2 cx), min(h, th) kept rows
+    MapDims dmax;
+    map_dims(std::min(h, th + 2 * cy), std::min(w, tw + 2 * cx), ny, nx, hk, wk, LP_OUT_SAME, &dmax);
+    dmax.Hout = std::min(h, th);
+    dmax.ldU = even_up(dmax.Hout);
+    dmax.prec = (int)prec;
+    void* ws = nullptr;
+    if ((st = lp_get_workspace(ctx, s, lp_workspace_bytes(dmax, n), &ws)) != LP_OK) return st;
+    std::vector<float*> o(n);
+    for (int a = 0; a < h; a += th) {
+        const int ra = std::max(0, a - cy), rb = std::min(h, a + th + cy);
+        for (int b = 0; b < w; b += tw) {
+            const int ca = std::max(0, b - cx), cb = std::min(w, b + tw + cx);
+            MapDims d;
+            map_dims(rb - ra, cb - ca, ny, nx, hk, wk, LP_OUT_SAME, &d);
+            d.Hout = std::min(th, h - a);
+            d.Wout = std::min(tw, w - b);
+            d.r0 = a - ra;
+            d.c0 = b - ca;
+            d.ldU = even_up(d.Hout);
+            d.prec = (int)prec;
+            for (int k = 0; k < n; ++k) o[k] = out[k] + (size_t)a * ldo + b;
+            st = lp_launch_map(ctx, L + (size_t)ra * ldl + ca, rb - ra, cb - ca, ldl, spectra, n, o.data(), ldo, d,
+                               ws, s);
+            if (st != LP_OK) return st;
+        }
+    }
+    return LP_OK;
 }
 
 // Host-buffer map, pipelined in row bands: the map is copied up band by band

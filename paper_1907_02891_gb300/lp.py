@@ -32,7 +32,7 @@ EXPORTS = (
     "lp_version", "lp_last_error", "lp_create", "lp_destroy", "lp_bytes_in_use",
     "lp_num_supported_sizes", "lp_supported_size_at", "lp_supported_size", "lp_split_supported",
     "lp_kernel_spectrum", "lp_spectrum_info", "lp_spectrum_copy", "lp_spectrum_release",
-    "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_workspace_bytes", "lp_sync_status",
+    "lp_map", "lp_map_host", "lp_map_multiclass", "lp_map_tiled", "lp_tiled_pad", "lp_map_workspace_bytes", "lp_sync_status",
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
     "lp_set_test_hook",
     "lp_serve_start", "lp_serve_submit", "lp_serve_poll", "lp_serve_stats", "lp_serve_stop",
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lp_spectrum_release": ([_vp, _vp], _i),
         "lp_map": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp], _i),
         "lp_map_host": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp], _i),
+        "lp_map_tiled": ([_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _i, _vp], _i),
+        "lp_tiled_pad": ([_i, _i, _i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
         "lp_map_multiclass": ([_vp, _vp, _i, _i, _i, _i, _vp, _vp, _i, _i, _i, _vp], _i),
         "lp_map_workspace_bytes": ([_i, _i, _i, _i, _i, _i, _i, _i], _sz),
         "lp_sync_status": ([_vp, _vp, _i], _i),
@@ -210,6 +212,29 @@ def lp_map(ctx: int, L, spectra: Sequence[int], out: Sequence, mode: int = LP_OU
     _check(load_library().lp_map(ctx, L.data_ptr(), h, w, L.stride(0), _ptr_array(spectra),
                                  len(spectra), _ptr_array([o.data_ptr() for o in out]), ldo,
                                  mode, prec, _stream_handle(stream)), "lp_map")
+
+
+def lp_map_tiled(ctx: int, L, spectra: Sequence[int], out: Sequence, prec: int = LP_PREC_FP32,
+                 stream=None) -> None:
+    """SAME-mode map of any size in overlap-save tiles of (Ny - hk + 1) x
+    (Nx - wk + 1) output pixels; tensors as lp_map."""
+    h, w = L.shape
+    if L.stride(1) != 1 or any(o.stride(1) != 1 for o in out):
+        raise ValueError("rows must be contiguous")
+    ldo = out[0].stride(0)
+    if any(o.stride(0) != ldo for o in out):
+        raise ValueError("all outputs need the same row stride")
+    _check(load_library().lp_map_tiled(ctx, L.data_ptr(), h, w, L.stride(0), _ptr_array(spectra),
+                                       len(spectra), _ptr_array([o.data_ptr() for o in out]), ldo,
+                                       prec, _stream_handle(stream)), "lp_map_tiled")
+
+
+def lp_tiled_pad(h: int, w: int, hk: int, wk: int, prec: int = LP_PREC_FP32):
+    """(pad_ny, pad_nx) that lp_map_tiled maps an h x w map with the fewest
+    transformed points (host only)."""
+    ny, nx = _i(), _i()
+    _check(load_library().lp_tiled_pad(h, w, hk, wk, prec, ctypes.byref(ny), ctypes.byref(nx)), "lp_tiled_pad")
+    return ny.value, nx.value
 
 
 def lp_map_host(ctx: int, L: np.ndarray, spectra: Sequence[int], out: Sequence[np.ndarray],

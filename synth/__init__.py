@@ -163,6 +163,10 @@ WORKLOADS = {
     "map16384_psf801": Workload("map16384_psf801", 16384, 16384, 0.742, 6400, 0.05,
                                 (1e-3, 1e3), (1e-3, 1e3), 801, ((0.1, 1.25, 80.0),),
                                 BASE_SEED + 3),
+    # 17800 x 21000 map (longer than the longest FFT length): the tiled form,
+    # same generator and PSF as the 16384^2 workload
+    "map17800x21000_psf801": Workload("map17800x21000_psf801", 17800, 21000, 0.742, 8900, 0.05,
+                                      None, None, 801, ((0.1, 1.25, 80.0),), BASE_SEED + 6),
 }
 
 # The paper's own shape (Sec. 3): an 11920 x 11804 map of 404.4 m pixels and

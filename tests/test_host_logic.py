@@ -75,6 +75,14 @@ def test_fingerprint_ignores_notes_but_not_knobs(tmp_path, monkeypatch):
     alt["4704"] = dict(e, minb=[3, 3, 3])
     p.write_text(json.dumps(alt))
     assert bench.kernel_source_sha(lengths=(4704,)) != base
+    monkeypatch.setattr(bench, "TUNED_PLANS", os.path.relpath(B.TUNED_JSON, bench.ROOT))
+    assert bench.kernel_source_sha(lengths=(4704,)) == base
+    # the generated sources' template and the compiler flags are part of it
+    monkeypatch.setattr(B, "NVCC_FLAGS", B.NVCC_FLAGS + ["-DX"])
+    assert bench.kernel_source_sha(lengths=(4704,)) != base
+    monkeypatch.undo()
+    monkeypatch.setattr(B, "_SIZE_TU", B._SIZE_TU + "\n")
+    assert bench.kernel_source_sha(lengths=(4704,)) != base
 
 
 def test_tune_cache_env_names_the_plan_file(tmp_path, monkeypatch):

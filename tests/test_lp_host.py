@@ -83,3 +83,36 @@ def test_no_gpu_errors_are_reported_not_raised(lib):
     assert st == lp.LP_ERR_CUDA and ctx.value is None
     assert b"no CUDA device" in lib.lp_last_error()
     assert lib.lp_create(None, 0, 0) == lp.LP_ERR_INVALID
+
+
+def test_tiled_pad_minimises_transformed_points(lib):
+    """lp_tiled_pad against a brute-force search of the size table: per
+    dimension the length N >= k with the fewest points ceil(n / (N - k + 1))
+    N over all tiles (ties: fewer tiles); maps one transform holds keep the
+    lp_map padding."""
+    from paper_1907_02891_gb300 import lp
+    sizes = lp.supported_sizes()
+
+    def brute(n, k, split=False):
+        best = None
+        for N in sizes:
+            if N < k or (split and not lp.lp_split_supported(N)):
+                continue
+            tiles = -(-n // (N - k + 1))
+            key = (tiles * N, tiles)
+            if best is None or key < best[0]:
+                best = (key, N)
+        return best[1]
+
+    for h, w, hk, wk in ((17800, 21000, 801, 801), (100000, 3000, 1485, 965), (300, 260, 31, 31),
+                         (1, 1, 1, 1), (5000, 40000, 541, 1), (65, 65, 63, 63)):
+        assert lp.lp_tiled_pad(h, w, hk, wk) == (brute(h, hk), brute(w, wk)), (h, w, hk, wk)
+        assert lp.lp_tiled_pad(h, w, hk, wk, lp.LP_PREC_SPLIT_BF16)[0] == brute(h, hk, True)
+    for side, k in ((256, 101), (4096, 541), (8192, 601), (16384, 801)):
+        n = lp.lp_supported_size(side + k - 1)
+        assert lp.lp_tiled_pad(side, side, k, k) == (n, n)
+    for bad in ((0, 10, 3, 3), (10, 10, 4, 3), (10, 10, 3, -1)):
+        with pytest.raises(lp.LpError):
+            lp.lp_tiled_pad(*bad)
+    with pytest.raises(lp.LpError):   # no supported length holds the PSF
+        lp.lp_tiled_pad(10, 10, 2 * max(sizes) + 1, 3)
