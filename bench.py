@@ -70,10 +70,11 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-log", default=None,
                     help="--mode serve: append one JSON line per request to this file")
-    ap.add_argument("--forms", default="batched,split_bf16,tiled,serve",
+    ap.add_argument("--forms", default="batched,split_bf16,tiled,graph,serve",
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
                          "tiled (17800 x 21000, 801^2 PSF, overlap-save tiles), "
+                         "graph (64 maps of 256^2 as one CUDA-graph replay), "
                          "serve (Poisson requests at 130%% and at 70%% load)")
     ap.add_argument("--forms-serve-requests", type=int, default=400)
     return ap.parse_args()
@@ -621,6 +622,73 @@ def _form_tiled(lp, args, wl, flush, stream, dev):
         lp.lp_destroy(ctx)
 
 
+def _form_graph(lp, args, flush, stream, dev, n_maps=64):
+    """The launch-bound form: a loop of n_maps small maps (the 256^2 map with
+    the 101^2 PSF, each its own input and output) as direct lp_map_noalloc
+    calls and as one replay of the same calls captured into a CUDA graph;
+    device time per loop by CUDA events, L2 flushed before each loop."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    wl = synth.WORKLOADS["map256_psf101"]
+    K = wl.psfs()[0]
+    ctx = lp.lp_create(dev.index or 0)
+    try:
+        spec = lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), max_h=wl.H, max_w=wl.W)
+        lp.lp_sync_status(ctx)
+        Ls = [torch.from_numpy(synth.radiance_map(wl.H, wl.W, wl.n_cities, wl.seed + 500 + i)).to(dev)
+              for i in range(n_maps)]
+        outs = [torch.empty_like(L) for L in Ls]
+        s = torch.cuda.Stream()
+
+        def loop():
+            for L, o in zip(Ls, outs):
+                lp.lp_map_noalloc(ctx, L, [spec], [o])
+
+        with torch.cuda.stream(s):
+            loop()
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            loop()
+        steps = max(3, min(args.steps, 20))
+
+        def timed(fn):
+            ts = []
+            with torch.cuda.stream(s):
+                for k in range(steps + 3):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(s)
+                    fn()
+                    b.record(s)
+                    b.synchronize()
+                    if k >= 3:
+                        ts.append(a.elapsed_time(b))
+            return statistics.mean(ts)
+
+        ms_direct = timed(loop)
+        ms_graph = timed(g.replay)
+        B = outs[0].cpu().numpy().astype(np.float64)
+        ref = oracle.conv_same(Ls[0].cpu().numpy(), K)
+        err = float(np.max(np.abs(B - ref)) / np.max(np.abs(ref)))
+        px = wl.H * wl.W * n_maps
+        rec = {"workload": wl.name, "map": f"{wl.H}x{wl.W}", "psf": f"{wl.psf_side}x{wl.psf_side}",
+               "maps_per_step": n_maps, "kernels_per_step": 3 * n_maps, "steps": steps,
+               "mpix_s": px / (ms_graph / 1e3) / 1e6, "ms_per_step": ms_graph,
+               "direct": {"mpix_s": px / (ms_direct / 1e3) / 1e6, "ms_per_step": ms_direct,
+                          "what": "the same lp_map_noalloc calls launched one by one"},
+               "speedup_vs_direct": ms_direct / ms_graph, "max_norm_err": err, "tolerance": 1e-5,
+               "what": "one CUDA-graph replay of the captured calls"}
+        del g
+        lp.lp_spectrum_release(ctx, spec)
+        lp.lp_sync_status(ctx)
+        return rec
+    finally:
+        lp.lp_destroy(ctx)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -766,6 +834,8 @@ def run_ours(args, rank, world, local_rank):
         if "split_bf16" in want:
             forms["split_bf16"] = _form_map(lp, args, synth.WORKLOADS["map16384_psf801"], "split_bf16",
                                             flush, stream, dev)
+        if "graph" in want:
+            forms["graph"] = _form_graph(lp, args, flush, stream, dev)
         if "tiled" in want:
             forms["tiled"] = _form_tiled(lp, args, synth.WORKLOADS["map17800x21000_psf801"], flush, stream, dev)
         if "serve" in want:

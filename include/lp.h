@@ -54,7 +54,8 @@ typedef enum lp_status {
     LP_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
     LP_ERR_UNSUPPORTED = 5, /* size or precision not built into this library */
     LP_ERR_BUSY = 6,        /* serving queue full / state does not allow the call */
-    LP_ERR_DEVICE = 7       /* a kernel reported an anomaly in the device status word */
+    LP_ERR_DEVICE = 7,      /* a kernel reported an anomaly in the device status word */
+    LP_ERR_CANCELLED = 8    /* a queued serving request was cancelled before it started */
 } lp_status;
 
 typedef enum lp_precision {
@@ -238,6 +239,22 @@ lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T, int h, in
  *     calls (every scratch element read is first written by the same call).
  */
 #define LP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/*
+ * CUDA graphs (no counterpart in the paper).  lp_map_noalloc, lp_map and
+ * lp_map_tiled may be called on a stream that is being captured into a CUDA
+ * graph (cudaStreamBeginCapture, any capture mode); the call then only
+ * enqueues its kernels, so a loop of maps replays as one graph launch.
+ * Conditions, each an LP_ERR_INVALID before anything is enqueued: every
+ * spectrum's build has completed and been seen complete by an earlier
+ * uncaptured map call (make one such call after lp_sync_status); pass
+ * timing is off; lp_map and lp_map_tiled need their stream's workspace to
+ * be large enough already (the same call once before capturing), since
+ * growing it would allocate.  While capturing, the library neither frees
+ * released spectra nor records their use, and it does not see the graph's
+ * replays: keep L, out[] and the spectra alive while the graph may run.
+ * lp_map_host cannot be captured (LP_ERR_INVALID).
+ */
 lp_status lp_map_noalloc(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                          const lp_spectrum* const* spectra, int n, float* const* out, int ldo,
                          lp_outmode mode, lp_precision prec, void* stream);
@@ -269,6 +286,10 @@ lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
 /* LP_TEST_FP_COLLIDE: every PSF gets the same cache fingerprint, so that
  * the value comparison that confirms a cache hit is what tells PSFs apart. */
 #define LP_TEST_FP_COLLIDE 2
+/* LP_TEST_SERVE_FAIL: the serving scheduler fails the next request it
+ * admits as if its launch had failed (LP_ERR_CUDA, from the host: no kernel
+ * runs), then clears the bit; the other requests are unaffected. */
+#define LP_TEST_SERVE_FAIL 4
 lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
 
 /*
@@ -332,6 +353,15 @@ lp_status lp_serve_poll(lp_ctx* ctx, uint64_t ticket, int timeout_ms, double* la
 lp_status lp_serve_stats(lp_ctx* ctx, uint64_t* completed, uint64_t* failed, int* queued,
                          int* running);
 lp_status lp_serve_stop(lp_ctx* ctx);
+
+/*
+ * Cancel a queued request: LP_OK if it had not started (it never runs, its
+ * spectrum references are dropped, and lp_serve_poll then returns
+ * LP_ERR_CANCELLED for it), LP_ERR_BUSY if it is already running or
+ * finished (work on the GPU is not interrupted), LP_ERR_INVALID for an
+ * unknown ticket.
+ */
+lp_status lp_serve_cancel(lp_ctx* ctx, uint64_t ticket);
 
 /*
  * Per-request log of the serving loop (metrics; no counterpart in the

@@ -368,6 +368,16 @@ lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out)
 }
 
 // per-stream workspace; grows (with a device sync) when a call needs more
+bool lp_stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out)
 {
     std::lock_guard<std::mutex> g(ctx->ws_mu);
@@ -379,6 +389,13 @@ lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out
         w = &ctx->ws.back();
     }
     if (w->bytes < bytes) {
+        // growing synchronises the stream and allocates: neither may happen
+        // inside a stream capture
+        if (lp_stream_capturing(s))
+            return lp_fail(LP_ERR_INVALID,
+                           "workspace of %zu bytes needed while the stream is being captured (%zu held): "
+                           "run the same call once before capturing, or use lp_map_noalloc",
+                           bytes, w->bytes);
         if (w->ptr) {
             cudaStreamSynchronize(s);
             lp_ctx_free(ctx, w->ptr, w->bytes);
@@ -1065,7 +1082,21 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     float2* U = T + (size_t)d.ncolsT * d.ldT;
     const int nchunk = n < kMaxSpectraPerLaunch ? n : kMaxSpectraPerLaunch;
     float2* park = uses_park(d, nchunk) ? park_of(d, U, nchunk) : nullptr;
-    if ((ps = lp_wait_spectra_built(spectra, n, st)) != LP_OK) return ps;
+    // Inside a stream capture (a CUDA graph) the map may only launch
+    // kernels: no spectrum build may still be pending (a wait on it would tie
+    // the graph to that one build), no pass events, and no use events (the
+    // library does not see the graph's replays; the caller keeps the spectra
+    // alive while the graph may run).
+    const bool capturing = lp_stream_capturing(st);
+    if (capturing) {
+        for (int k = 0; k < n; ++k)
+            if (!spectra[k]->built.load(std::memory_order_acquire) && cudaEventQuery(spectra[k]->ready) != cudaSuccess)
+                return lp_fail(LP_ERR_INVALID, "spectrum %d is still being built: synchronise before capturing", k);
+        std::lock_guard<std::mutex> g(ctx->tim_mu);
+        if (ctx->timing) return lp_fail(LP_ERR_INVALID, "pass timing is on: switch it off before capturing");
+    } else if ((ps = lp_wait_spectra_built(spectra, n, st)) != LP_OK) {
+        return ps;
+    }
     if ((ps = launch_rows_forward(ctx, px, L, h, w, ldl, d, T, 0, (int)(d.ldT / 2), st)) != LP_OK) return ps;
     for (int base = 0; base < n; base += kMaxSpectraPerLaunch) {
         const int cnt = (n - base) < kMaxSpectraPerLaunch ? (n - base) : kMaxSpectraPerLaunch;
@@ -1075,7 +1106,7 @@ lp_status lp_launch_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     }
     // recorded after the last pass (an event between the passes would stop
     // the next pass's launch from overlapping the previous one's tail)
-    lp_note_spectra_used(ctx, spectra, n, st);
+    if (!capturing) lp_note_spectra_used(ctx, spectra, n, st);
     return LP_OK;
 }
 
@@ -1095,8 +1126,8 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
         if (o0 < l1 && l0 < o1) return lp_fail(LP_ERR_INVALID, "lp_map: out[%d] overlaps L", k);
     }
     DeviceGuard dg(ctx->device);
-    lp_reap_released(ctx, false);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!lp_stream_capturing(s)) lp_reap_released(ctx, false);  // frees memory: not inside a capture
     const lp_spectrum* s0 = spectra[0];
     void* ws = nullptr;
     st = lp_get_workspace(ctx, s, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
@@ -1142,8 +1173,8 @@ extern "C" lp_status lp_map_tiled(lp_ctx* ctx, const float* L, int h, int w, int
         if (o0 < l1 && l0 < o1) return lp_fail(LP_ERR_INVALID, "lp_map_tiled: out[%d] overlaps L", k);
     }
     DeviceGuard dg(ctx->device);
-    lp_reap_released(ctx, false);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!lp_stream_capturing(s)) lp_reap_released(ctx, false);  // frees memory: not inside a capture
     // one workspace for the largest tile: window min(h, th + 2 cy) x
     // min(w, tw + 2 cx), min(h, th) kept rows
     MapDims dmax;
@@ -1222,6 +1253,8 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
         if (!out_host[k]) return lp_fail(LP_ERR_INVALID, "lp_map_host: out[%d] is NULL", k);
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (lp_stream_capturing(s))
+        return lp_fail(LP_ERR_INVALID, "lp_map_host: host copies on internal streams cannot be captured");
     const lp_spectrum* s0 = spectra[0];
     const PlanRec *py, *px;
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
@@ -1334,7 +1367,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
 extern "C" lp_status lp_set_test_hook(lp_ctx* ctx, int hook)
 {
     if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: NULL context");
-    if (hook & ~(LP_TEST_TC_NO_MMA | LP_TEST_FP_COLLIDE))
+    if (hook & ~(LP_TEST_TC_NO_MMA | LP_TEST_FP_COLLIDE | LP_TEST_SERVE_FAIL))
         return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: unknown hook 0x%x", hook);
     ctx->test_hook = hook;
     return LP_OK;

@@ -102,7 +102,7 @@ struct lp_ctx {
     void* staging = nullptr;
     size_t staging_bytes = 0;
     int* d_err = nullptr;  // sticky device status word
-    int test_hook = 0;     // lp_set_test_hook bits
+    std::atomic<int> test_hook{0};  // lp_set_test_hook bits (read by the serving thread too)
     ServeState* serve = nullptr;
     // pass timing
     std::mutex tim_mu;
@@ -125,6 +125,8 @@ lp_status lp_ctx_alloc(lp_ctx* ctx, size_t bytes, void** p);
 void lp_ctx_free(lp_ctx* ctx, void* p, size_t bytes);
 lp_status lp_get_plan(lp_ctx* ctx, int N, const PlanRec** out);
 lp_status lp_get_workspace(lp_ctx* ctx, cudaStream_t s, size_t bytes, void** out);
+// true while stream s is being captured into a CUDA graph
+bool lp_stream_capturing(cudaStream_t s);
 lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
                           const lp_spectrum* const* spectra, int n, const void* out, int ldo,
                           lp_outmode mode, lp_precision prec, MapDims* d);

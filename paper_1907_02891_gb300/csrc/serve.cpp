@@ -148,6 +148,9 @@ static void scheduler_loop(ServeState* S)
             Slot& sl = *free_slot;
             void* ws = nullptr;
             lp_status st = lp_get_workspace(S->ctx, sl.stream, rq.footprint, &ws);
+            // failure injection (host side): this request fails as a launch would
+            if (st == LP_OK && (S->ctx->test_hook.fetch_and(~LP_TEST_SERVE_FAIL) & LP_TEST_SERVE_FAIL))
+                st = lp_fail(LP_ERR_CUDA, "injected launch failure (LP_TEST_SERVE_FAIL)");
             if (st == LP_OK)
                 st = lp_launch_map(S->ctx, rq.L, rq.h, rq.w, rq.ldl, rq.spectra.data(), (int)rq.spectra.size(),
                                    rq.out.data(), rq.ldo, rq.dims, ws, sl.stream);
@@ -295,6 +298,34 @@ extern "C" lp_status lp_serve_stats(lp_ctx* ctx, uint64_t* completed, uint64_t* 
         for (auto& sl : S->slots) r += sl.busy ? 1 : 0;
         *running = r;
     }
+    return LP_OK;
+}
+
+extern "C" lp_status lp_serve_cancel(lp_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_serve_cancel: NULL context");
+    ServeState* S = ctx->serve;
+    if (!S) return lp_fail(LP_ERR_BUSY, "lp_serve_cancel: serving not started");
+    std::vector<const lp_spectrum*> refs;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (ticket == 0 || ticket >= S->next_ticket)
+            return lp_fail(LP_ERR_INVALID, "lp_serve_cancel: unknown ticket");
+        auto it = S->queue.begin();
+        while (it != S->queue.end() && it->ticket != ticket) ++it;
+        if (it == S->queue.end())
+            return lp_fail(LP_ERR_BUSY, "lp_serve_cancel: request %llu is running or finished",
+                           (unsigned long long)ticket);
+        refs.swap(it->spectra);
+        S->queue.erase(it);
+        Result r;
+        r.status = LP_ERR_CANCELLED;
+        r.latency_ms = 0.0;
+        r.queue_ms = 0.0;
+        S->done[ticket] = r;
+    }
+    for (const lp_spectrum* sp : refs) lp_spectrum_unref(ctx, sp);
+    S->cv_done.notify_all();
     return LP_OK;
 }
 

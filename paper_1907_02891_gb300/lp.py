@@ -19,13 +19,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
 
 LP_OK, LP_ERR_INVALID, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_TIMEOUT = 0, 1, 2, 3, 4
-LP_ERR_UNSUPPORTED, LP_ERR_BUSY, LP_ERR_DEVICE = 5, 6, 7
+LP_ERR_UNSUPPORTED, LP_ERR_BUSY, LP_ERR_DEVICE, LP_ERR_CANCELLED = 5, 6, 7, 8
 LP_PREC_FP32, LP_PREC_SPLIT_BF16, LP_PREC_SPLIT_FP16 = 0, 1, 2
 LP_OUT_SAME, LP_OUT_FULL = 0, 1
 
 STATUS_NAMES = {0: "LP_OK", 1: "LP_ERR_INVALID", 2: "LP_ERR_OOM", 3: "LP_ERR_CUDA",
                 4: "LP_ERR_TIMEOUT", 5: "LP_ERR_UNSUPPORTED", 6: "LP_ERR_BUSY",
-                7: "LP_ERR_DEVICE"}
+                7: "LP_ERR_DEVICE", 8: "LP_ERR_CANCELLED"}
 
 # every entry point declared in include/lp.h
 EXPORTS = (
@@ -36,7 +36,7 @@ EXPORTS = (
     "lp_set_pass_timing", "lp_get_pass_timing", "lp_map_noalloc", "lp_map_noalloc_scratch_bytes",
     "lp_set_test_hook",
     "lp_serve_start", "lp_serve_submit", "lp_serve_poll", "lp_serve_stats", "lp_serve_stop",
-    "lp_serve_log",
+    "lp_serve_log", "lp_serve_cancel",
 )
 
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                             ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
         "lp_serve_stop": ([_vp], _i),
         "lp_serve_log": ([_vp, ctypes.c_char_p], _i),
+        "lp_serve_cancel": ([_vp, ctypes.c_uint64], _i),
         "lp_get_pass_timing": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
@@ -291,6 +292,7 @@ PASS_NAMES = ("p1_rows", "p2_cols", "p3_rows")
 
 LP_TEST_TC_NO_MMA = 1
 LP_TEST_FP_COLLIDE = 2
+LP_TEST_SERVE_FAIL = 4
 
 
 def lp_set_test_hook(ctx: int, hook: int) -> None:
@@ -375,6 +377,12 @@ def lp_serve_stats(ctx: int) -> dict:
 def lp_serve_log(ctx: int, path) -> None:
     """Append one JSON line per finished request to path (None: stop logging)."""
     _check(load_library().lp_serve_log(ctx, None if path is None else str(path).encode()), "lp_serve_log")
+
+
+def lp_serve_cancel(ctx: int, ticket: int) -> None:
+    """Cancel a queued request (raises LpError with LP_ERR_BUSY if it is
+    already running or finished)."""
+    _check(load_library().lp_serve_cancel(ctx, ticket), "lp_serve_cancel")
 
 
 def lp_serve_stop(ctx: int) -> None:

@@ -247,3 +247,93 @@ def test_request_log_lines(tmp_path):
             assert abs(r["latency_ms"] - lats[t]) < 1e-3
     finally:
         lp.lp_destroy(ctx)
+
+
+def test_cancel_a_queued_request():
+    """One slot, two long requests ahead: a request cancelled while queued
+    never runs (its output keeps its NaNs) and polls as LP_ERR_CANCELLED; a
+    running or finished one cannot be cancelled; the rest are unaffected."""
+    ctx = lp.lp_create(0)
+    try:
+        _, spectra = _bank(ctx, (8192, 256), n_psf=4, psf_side=201)
+        big = torch.from_numpy(synth.radiance_map(8192, 8192, 400, 21)).to(DEV)
+        small = torch.from_numpy(synth.radiance_map(256, 256, 8, 22)).to(DEV)
+        ref = torch.empty_like(small)
+        lp.lp_map(ctx, small, [spectra[(256, 0)]], [ref])
+        lp.lp_sync_status(ctx)
+        lp.lp_serve_start(ctx, 1)
+        bouts = [[torch.empty_like(big) for _ in range(4)] for _ in range(2)]
+        t_big = [lp.lp_serve_submit(ctx, big, [spectra[(8192, i)] for i in range(4)], o) for o in bouts]
+        o_cancel = torch.full_like(small, float("nan"))
+        o_keep = torch.full_like(small, float("nan"))
+        t_cancel = lp.lp_serve_submit(ctx, small, [spectra[(256, 0)]], [o_cancel])
+        t_keep = lp.lp_serve_submit(ctx, small, [spectra[(256, 0)]], [o_keep])
+        lp.lp_serve_cancel(ctx, t_cancel)
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_cancel(ctx, t_cancel)          # no longer queued
+        assert e.value.status == lp.LP_ERR_BUSY
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_cancel(ctx, 10 ** 9)
+        assert e.value.status == lp.LP_ERR_INVALID
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_poll(ctx, t_cancel, timeout_ms=1000)
+        assert e.value.status == lp.LP_ERR_CANCELLED
+        for t in t_big + [t_keep]:
+            assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+        with pytest.raises(lp.LpError) as e:
+            lp.lp_serve_cancel(ctx, t_big[0])          # finished
+        assert e.value.status == lp.LP_ERR_BUSY
+        st = lp.lp_serve_stats(ctx)
+        assert st["completed"] == 3 and st["failed"] == 0 and st["queued"] == 0
+        lp.lp_serve_stop(ctx)
+        assert torch.isnan(o_cancel).all()
+        assert torch.equal(o_keep, ref)
+    finally:
+        lp.lp_destroy(ctx)
+
+
+def test_injected_launch_failure_fails_one_request_only():
+    """LP_TEST_SERVE_FAIL (host-side injection): the next admitted request
+    fails with LP_ERR_CUDA and frees its slot; the others, before and after,
+    finish with the results they have alone."""
+    sides = (64, 256)
+    ctx = lp.lp_create(0)
+    try:
+        _, spectra = _bank(ctx, sides)
+        reqs = _requests(6, sides, 11)
+        alone = []
+        for s, ks, L in reqs:
+            o = [torch.empty((s, s), device=DEV) for _ in ks]
+            lp.lp_map(ctx, L, [spectra[(s, i)] for i in ks], o)
+            alone.append(o)
+        lp.lp_sync_status(ctx)
+        lp.lp_serve_start(ctx, 1)
+        outs, tickets = [], []
+        for r, (s, ks, L) in enumerate(reqs):
+            if r == 2:   # the first two have run; the next admitted request fails
+                for t in tickets:
+                    assert lp.lp_serve_poll(ctx, t, timeout_ms=60000) is not None
+                lp.lp_set_test_hook(ctx, lp.LP_TEST_SERVE_FAIL)
+            o = [torch.full((s, s), float("nan"), device=DEV) for _ in ks]
+            tickets.append(lp.lp_serve_submit(ctx, L, [spectra[(s, i)] for i in ks], o))
+            outs.append(o)
+        status = []
+        for t in tickets[2:]:
+            try:
+                lp.lp_serve_poll(ctx, t, timeout_ms=60000)
+                status.append(lp.LP_OK)
+            except lp.LpError as e:
+                status.append(e.status)
+        assert status == [lp.LP_ERR_CUDA, lp.LP_OK, lp.LP_OK, lp.LP_OK]
+        st = lp.lp_serve_stats(ctx)
+        assert st["failed"] == 1 and st["completed"] == 5
+        lp.lp_serve_stop(ctx)
+        for r, (a, b) in enumerate(zip(alone, outs)):
+            for x, y in zip(a, b):
+                if r == 2:
+                    assert torch.isnan(y).all()
+                else:
+                    assert torch.equal(x, y)
+    finally:
+        lp.lp_set_test_hook(ctx, 0)
+        lp.lp_destroy(ctx)

@@ -8,6 +8,8 @@ hide the rest of the suite; it passes alone in a fresh process and after the
 other tests.
 """
 
+import gc
+
 import numpy as np
 import pytest
 
@@ -118,10 +120,18 @@ def test_noalloc_allocates_nothing_on_a_fresh_stream():
         with torch.cuda.stream(s):
             torch.zeros(1, device=dev).add_(1)     # the stream's first work, outside the check
         torch.cuda.synchronize()
-        before = (lp.lp_bytes_in_use(ctx), torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
-        lp.lp_map_noalloc(ctx, Ld, specs, got, stream=s)
-        lp.lp_sync_status(ctx, stream=s)
-        after = (lp.lp_bytes_in_use(ctx), torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        # no garbage collection inside the window: a collection there frees
+        # tensors that earlier tests left in reference cycles, which moves
+        # torch's counter without any allocation by the call
+        gc.collect()
+        gc.disable()
+        try:
+            before = (lp.lp_bytes_in_use(ctx), torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+            lp.lp_map_noalloc(ctx, Ld, specs, got, stream=s)
+            lp.lp_sync_status(ctx, stream=s)
+            after = (lp.lp_bytes_in_use(ctx), torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        finally:
+            gc.enable()
         assert before[0] == after[0], "context memory changed"
         assert before[1] == after[1], "torch memory changed"
         assert abs(before[2] - after[2]) < (1 << 20), "device memory changed"
