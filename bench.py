@@ -74,7 +74,7 @@ def parse_args():
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
                          "tiled (17800 x 21000, 801^2 PSF, overlap-save tiles), "
-                         "graph (64 maps of 256^2 as one CUDA-graph replay), "
+                         "graph (loops of small maps as one CUDA-graph replay), "
                          "serve (Poisson requests at 130%% and at 70%% load)")
     ap.add_argument("--forms-serve-requests", type=int, default=400)
     return ap.parse_args()
@@ -622,23 +622,21 @@ def _form_tiled(lp, args, wl, flush, stream, dev):
         lp.lp_destroy(ctx)
 
 
-def _form_graph(lp, args, flush, stream, dev, n_maps=64):
-    """The launch-bound form: a loop of n_maps small maps (the 256^2 map with
-    the 101^2 PSF, each its own input and output) as direct lp_map_noalloc
-    calls and as one replay of the same calls captured into a CUDA graph;
-    device time per loop by CUDA events, L2 flushed before each loop."""
+def _graph_case(lp, flush, dev, side, psf, n_maps, steps, seed):
+    """n_maps maps of side^2 with one psf^2 PSF, each its own input and
+    output: direct lp_map_noalloc calls against one replay of the same calls
+    captured into a CUDA graph.  Device time per loop by CUDA events (L2
+    flushed before each loop) and host time to enqueue the loop."""
     import numpy as np
     import torch
     import oracle
     import synth
-    wl = synth.WORKLOADS["map256_psf101"]
-    K = wl.psfs()[0]
+    K = synth.psf_power_exp(psf, 1.0, 0.25, 1.25, 40.0)
     ctx = lp.lp_create(dev.index or 0)
     try:
-        spec = lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), max_h=wl.H, max_w=wl.W)
+        spec = lp.lp_kernel_spectrum(ctx, torch.from_numpy(K).to(dev), max_h=side, max_w=side)
         lp.lp_sync_status(ctx)
-        Ls = [torch.from_numpy(synth.radiance_map(wl.H, wl.W, wl.n_cities, wl.seed + 500 + i)).to(dev)
-              for i in range(n_maps)]
+        Ls = [torch.from_numpy(synth.radiance_map(side, side, 12, seed + i)).to(dev) for i in range(n_maps)]
         outs = [torch.empty_like(L) for L in Ls]
         s = torch.cuda.Stream()
 
@@ -652,41 +650,52 @@ def _form_graph(lp, args, flush, stream, dev, n_maps=64):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
             loop()
-        steps = max(3, min(args.steps, 20))
 
         def timed(fn):
-            ts = []
+            dev_ms, host_ms = [], []
             with torch.cuda.stream(s):
                 for k in range(steps + 3):
                     flush.zero_()
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(s)
+                    t0 = time.perf_counter()
                     fn()
+                    t1 = time.perf_counter()
                     b.record(s)
                     b.synchronize()
                     if k >= 3:
-                        ts.append(a.elapsed_time(b))
-            return statistics.mean(ts)
+                        dev_ms.append(a.elapsed_time(b))
+                        host_ms.append((t1 - t0) * 1e3)
+            return statistics.mean(dev_ms), statistics.mean(host_ms)
 
-        ms_direct = timed(loop)
-        ms_graph = timed(g.replay)
+        d_ms, d_host = timed(loop)
+        g_ms, g_host = timed(g.replay)
         B = outs[0].cpu().numpy().astype(np.float64)
         ref = oracle.conv_same(Ls[0].cpu().numpy(), K)
         err = float(np.max(np.abs(B - ref)) / np.max(np.abs(ref)))
-        px = wl.H * wl.W * n_maps
-        rec = {"workload": wl.name, "map": f"{wl.H}x{wl.W}", "psf": f"{wl.psf_side}x{wl.psf_side}",
-               "maps_per_step": n_maps, "kernels_per_step": 3 * n_maps, "steps": steps,
-               "mpix_s": px / (ms_graph / 1e3) / 1e6, "ms_per_step": ms_graph,
-               "direct": {"mpix_s": px / (ms_direct / 1e3) / 1e6, "ms_per_step": ms_direct,
-                          "what": "the same lp_map_noalloc calls launched one by one"},
-               "speedup_vs_direct": ms_direct / ms_graph, "max_norm_err": err, "tolerance": 1e-5,
-               "what": "one CUDA-graph replay of the captured calls"}
+        px = side * side * n_maps
         del g
         lp.lp_spectrum_release(ctx, spec)
         lp.lp_sync_status(ctx)
-        return rec
+        return {"map": f"{side}x{side}", "psf": f"{psf}x{psf}", "maps_per_step": n_maps,
+                "kernels_per_step": 3 * n_maps,
+                "graph": {"mpix_s": px / (g_ms / 1e3) / 1e6, "ms_per_step": g_ms, "host_ms_per_step": g_host},
+                "direct": {"mpix_s": px / (d_ms / 1e3) / 1e6, "ms_per_step": d_ms, "host_ms_per_step": d_host},
+                "speedup_vs_direct": d_ms / g_ms, "max_norm_err": err, "tolerance": 1e-5}
     finally:
         lp.lp_destroy(ctx)
+
+
+def _form_graph(lp, args, flush, stream, dev):
+    """The launch-bound form: loops of small maps as direct calls and as one
+    CUDA-graph replay, for 64^2 tiles (31^2 PSF) and for the 256^2 map with
+    the 101^2 PSF."""
+    steps = max(3, min(args.steps, 20))
+    return {"what": "lp_map_noalloc loops: launched one by one (direct) against one replay of the "
+                    "same calls captured into a CUDA graph (graph); device time by CUDA events, host "
+                    "time to enqueue",
+            "cases": [_graph_case(lp, flush, dev, 64, 31, 256, steps, 1907_02891 + 600),
+                      _graph_case(lp, flush, dev, 256, 101, 64, steps, 1907_02891 + 700)]}
 
 
 def run_ours(args, rank, world, local_rank):

@@ -290,6 +290,15 @@ lp_status lp_sync_status(lp_ctx* ctx, void* stream, int timeout_ms);
  * admits as if its launch had failed (LP_ERR_CUDA, from the host: no kernel
  * runs), then clears the bit; the other requests are unaffected. */
 #define LP_TEST_SERVE_FAIL 4
+/* LP_TEST_BOUNDS: the map calls declare their intermediate buffer T one
+ * column block shorter than it is.  In the debug build (LP_DEBUG=1, the
+ * library paper_1907_02891_gb300/_build/debug/liblp.so, which checks every
+ * work unit's extents in every buffer before touching global memory) the
+ * units of the last columns then fail their checks: they are skipped and
+ * set bit 3 of the device status word, so lp_sync_status reports
+ * LP_ERR_DEVICE; no access leaves the real buffer.  The release build
+ * compiles the checks away and ignores the hook. */
+#define LP_TEST_BOUNDS 8
 lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
 
 /*

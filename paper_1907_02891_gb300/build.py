@@ -28,6 +28,11 @@ OUT = os.path.join(HERE, "_build")
 GEN = os.path.join(OUT, "gen")
 OBJ = os.path.join(OUT, "obj")
 LIB = os.path.join(OUT, "liblp.so")
+# debug build (LP_DEBUG=1: the passes check every work unit's extents in
+# every buffer first and report a miss in the device status word); a
+# library of its own, loaded by lp.py when $LP_DEBUG is set
+DEBUG_OBJ = os.path.join(OUT, "debug", "obj")
+DEBUG_LIB = os.path.join(OUT, "debug", "liblp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
@@ -261,6 +266,7 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
             b.K[0] = a.K[i];
             b.nspec = 1;
             b.U = a.U + (long long)i * a.specU;
+            b.u_elems = a.u_elems - (long long)i * a.specU;
             cudaError_t e = p2(b, kreal, s);
             if (e != cudaSuccess) return e;
         }}
@@ -354,9 +360,17 @@ def _write_if_changed(path: str, text: str) -> None:
         fh.write(text)
 
 
-def generate() -> List[str]:
-    os.makedirs(GEN, exist_ok=True)
+def generate(sizes: Sequence[int] = ()) -> List[str]:
+    """Write one translation unit per supported length (all, or `sizes`)
+    and the registry of the lengths written; returns their paths.  A
+    subset goes to its own directory, so that it never replaces the
+    registry of the full build."""
     table = plan_table()
+    gen = GEN
+    if sizes:
+        table = {n: table[n] for n in sorted(set(sizes))}
+        gen = os.path.join(OUT, "gen_" + "_".join(map(str, table)))
+    os.makedirs(gen, exist_ok=True)
     files = []
     for n, p in table.items():
         r = list(p["radices"])
@@ -370,12 +384,12 @@ def generate() -> List[str]:
                                batch=_b(p.get("batch", True)),
                                kst2=_b(p.get("kst2", False)), packed=int(bool(p.get("packed", False))),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
-        path = os.path.join(GEN, f"size_{n}.cu")
+        path = os.path.join(gen, f"size_{n}.cu")
         _write_if_changed(path, text)
         files.append(path)
     decls = "\n".join(f"extern const SizeKernels kSize_{n};" for n in table)
     ptrs = ", ".join(f"&kSize_{n}" for n in table)
-    path = os.path.join(GEN, "registry.cu")
+    path = os.path.join(gen, "registry.cu")
     _write_if_changed(path, _REGISTRY_TU.format(decls=decls, ptrs=ptrs, count=len(table)))
     files.append(path)
     return files
@@ -387,14 +401,14 @@ def _headers() -> List[str]:
     return hs
 
 
-def _compile(src: str, deps_mtime: float) -> str:
+def _compile(src: str, deps_mtime: float, debug: bool = False) -> str:
     name = os.path.splitext(os.path.basename(src))[0]
     digest = hashlib.sha1(src.encode()).hexdigest()[:8]
-    obj = os.path.join(OBJ, f"{name}_{digest}.o")
+    obj = os.path.join(DEBUG_OBJ if debug else OBJ, f"{name}_{digest}.o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), deps_mtime):
         return obj
-    cmd = ["nvcc", *ARCH, *NVCC_FLAGS, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
-           "-c", src, "-o", obj + ".tmp"]
+    cmd = ["nvcc", *ARCH, *NVCC_FLAGS, *(["-DLP_DEBUG=1"] if debug else []), "-I", CSRC,
+           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -402,31 +416,35 @@ def _compile(src: str, deps_mtime: float) -> str:
     return obj
 
 
-def build(jobs: int = 0, verbose: bool = False) -> str:
+def build(jobs: int = 0, verbose: bool = False, debug: bool = False, sizes: Sequence[int] = ()) -> str:
     """Compile every CUDA/C++ source of the library for sm_103a and link
-    liblp.so.  Returns the library path."""
+    liblp.so (with debug, the bounds-checked library DEBUG_LIB, optionally
+    with only the FFT lengths `sizes`).  Returns the library path."""
+    if sizes and not debug:
+        raise ValueError("a subset of lengths is for the debug build only")
     if shutil.which("nvcc") is None:
         raise RuntimeError("nvcc not found on PATH")
-    os.makedirs(OBJ, exist_ok=True)
-    gen = generate()
+    obj_dir, lib = (DEBUG_OBJ, DEBUG_LIB) if debug else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
+    gen = generate(sizes)
     srcs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cpp"))]
     srcs += gen
     deps = max(os.path.getmtime(h) for h in _headers() + [os.path.abspath(__file__)])
     jobs = jobs or max(1, os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, deps), srcs))
-    if (not os.path.exists(LIB)) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, deps, debug), srcs))
+    if (not os.path.exists(lib)) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose=True)
+    build(verbose=True, debug="--debug" in sys.argv[1:])
     sys.exit(0)

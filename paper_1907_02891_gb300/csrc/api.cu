@@ -930,6 +930,18 @@ lp_status lp_validate_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
     return LP_OK;
 }
 
+// Declared extents for the debug builds' bounds checks: T holds ncolsT x ldT
+// complex elements; LP_TEST_BOUNDS declares it one column block short, so
+// that the checks of the units touching the last columns fire (the
+// accesses stay inside the real buffer: nothing out of bounds happens).
+static long long t_extent(const lp_ctx* ctx, const MapDims& d)
+{
+    const long long cols = (ctx->test_hook.load() & LP_TEST_BOUNDS) ? d.ncolsT - 2 : d.ncolsT;
+    return cols * d.ldT;
+}
+
+static long long k_extent(const lp_spectrum* s) { return (long long)(s->bytes / (s->is_real ? 4 : 8)); }
+
 // The three passes as separate launches (row pairs [pair0, pair1) for the
 // row passes), composed by lp_launch_map and by the banded host-buffer map.
 static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float* L, int h, int w, int ldl,
@@ -948,6 +960,8 @@ static lp_status launch_rows_forward(lp_ctx* ctx, const PlanRec* px, const float
     a1.npairs = pair1;
     a1.ncols = d.ncols;
     a1.tw = px->fwd;
+    a1.err = ctx->d_err;
+    a1.t_elems = t_extent(ctx, d);
     const int tok = lp_pass_begin(ctx, 0, st);
     CUDA_TRY(px->k->p1(a1, st));
     lp_pass_end(ctx, tok, st);
@@ -995,6 +1009,11 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
             b.twi = py->rev;
             b.park = nullptr;
             b.ahead = 0;
+            b.err = ctx->d_err;
+            b.t_elems = t_extent(ctx, d);
+            b.u_elems = (long long)d.ncolsU * d.ldU;
+            b.k_elems = k_extent(spectra[base + i]);
+            b.park_elems = 0;
             a2.tables = static_cast<const uint4*>(py->tc_tables);
             a2.err = ctx->d_err;
             a2.no_mma = (ctx->test_hook & LP_TEST_TC_NO_MMA) ? 1 : 0;
@@ -1030,6 +1049,12 @@ static lp_status launch_columns(lp_ctx* ctx, const PlanRec* py, const lp_spectru
         a2.twi = py->rev;
         a2.park = park;
         a2.ahead = prefetch_ahead(ctx);
+        a2.err = ctx->d_err;
+        a2.t_elems = t_extent(ctx, d);
+        a2.u_elems = (long long)(cnt - k0) * d.ncolsU * d.ldU;
+        a2.k_elems = k_extent(spectra[base + k0]);
+        for (int i = k0 + 1; i < k1; ++i) a2.k_elems = std::min(a2.k_elems, k_extent(spectra[base + i]));
+        a2.park_elems = park ? (long long)(lp_park_bytes(d) / 8) : 0;
         const int tok = lp_pass_begin(ctx, 1, st);
         CUDA_TRY(py->k->p2(a2, kind != 0, st));
         lp_pass_end(ctx, tok, st);
@@ -1054,6 +1079,8 @@ static lp_status launch_rows_inverse(lp_ctx* ctx, const PlanRec* px, const MapDi
     a3.Wout = d.Wout;
     a3.ncols = d.ncols;
     a3.tw = px->rev;
+    a3.err = ctx->d_err;
+    a3.u_elems = (long long)cnt * d.ncolsU * d.ldU;
     const int tok = lp_pass_begin(ctx, 2, st);
     CUDA_TRY(px->k->p3(a3, cnt, st));
     lp_pass_end(ctx, tok, st);
@@ -1367,7 +1394,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
 extern "C" lp_status lp_set_test_hook(lp_ctx* ctx, int hook)
 {
     if (!ctx) return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: NULL context");
-    if (hook & ~(LP_TEST_TC_NO_MMA | LP_TEST_FP_COLLIDE | LP_TEST_SERVE_FAIL))
+    if (hook & ~(LP_TEST_TC_NO_MMA | LP_TEST_FP_COLLIDE | LP_TEST_SERVE_FAIL | LP_TEST_BOUNDS))
         return lp_fail(LP_ERR_INVALID, "lp_set_test_hook: unknown hook 0x%x", hook);
     ctx->test_hook = hook;
     return LP_OK;
@@ -1451,6 +1478,8 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
         a1.npairs = npairs;
         a1.ncols = d.ncols;
         a1.tw = px->fwd;
+        a1.err = ctx->d_err;
+        a1.t_elems = t_extent(ctx, d);
         CUDA_TRY(px->k->p1(a1, s));
     }
     // the real-spectrum kernel needs every class's spectrum real
@@ -1479,6 +1508,12 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a2.twf = py->fwd;
     a2.twi = py->rev;
     a2.acc = accb;
+    a2.err = ctx->d_err;
+    a2.t_elems = t_extent(ctx, d);
+    a2.k_elems = k_extent(spectra[0]);
+    for (int t = 1; t < T; ++t) a2.k_elems = std::min(a2.k_elems, k_extent(spectra[t]));
+    a2.u_elems = (long long)d.ncolsU * d.ldU;
+    a2.acc_elems = (long long)d.ncols * d.ny;
     {
         const cudaError_t e = py->k->p2m(a2, all_real, s);
         if (e != cudaSuccess) return lp_fail(LP_ERR_CUDA, "lp_map_multiclass: %s", cudaGetErrorString(e));
@@ -1496,6 +1531,8 @@ extern "C" lp_status lp_map_multiclass(lp_ctx* ctx, const float* const* L, int T
     a3.Wout = d.Wout;
     a3.ncols = d.ncols;
     a3.tw = px->rev;
+    a3.err = ctx->d_err;
+    a3.u_elems = (long long)d.ncolsU * d.ldU;
     CUDA_TRY(px->k->p3(a3, 1, s));
     lp_note_spectra_used(ctx, spectra, T, s);
     return LP_OK;

@@ -95,6 +95,8 @@ struct P1Args {
     int npairs;  // ceil(H/2)
     int ncols;   // Nx/2 + 1
     TwChain tw;  // forward chain of the row plan
+    int* err;            // device status word (debug builds: bounds checks)
+    long long t_elems;   // float2 elements of the T buffer
 };
 
 struct P2Args {
@@ -114,6 +116,11 @@ struct P2Args {
     TwChain twf, twi;  // forward and reversed chains of the column plan
     float2* park;      // batched pass: forward column spectra, N per column
     int ahead;         // column distance of the T prefetch into L2 (0: none)
+    int* err;              // device status word (debug builds: bounds checks)
+    long long t_elems;     // float2 elements of the T buffer
+    long long u_elems;     // float2 elements of U from a.U on (all spectra of the launch)
+    long long k_elems;     // spectrum values (floats or float2) of each spectrum
+    long long park_elems;  // float2 elements of the park area (0 without one)
 };
 
 struct P3Args {
@@ -128,7 +135,85 @@ struct P3Args {
     int Wout;
     int ncols;
     TwChain tw;  // reversed chain of the row plan
+    int* err;           // device status word (debug builds: bounds checks)
+    long long u_elems;  // float2 elements of U from a.U on (all spectra of the launch)
 };
+
+// Debug builds (LP_DEBUG=1, a library of their own): before a work unit
+// touches global memory, its block checks the unit's whole extent in every
+// buffer against the sizes the host passed; a unit outside them sets bit 3
+// of the device status word and is skipped (no assert or trap, so the
+// context stays usable).  Release builds compile the checks away.
+#ifndef LP_DEBUG
+#define LP_DEBUG 0
+#endif
+constexpr int kDevErrBounds = 8;
+
+__device__ __forceinline__ bool lp_checked(int* err, bool ok)
+{
+#if LP_DEBUG
+    if (!ok && threadIdx.x == 0) atomicOr(err, kDevErrBounds);
+    return ok;
+#else
+    (void)err;
+    (void)ok;
+    return true;
+#endif
+}
+
+// P1 unit: rows 2 pair, 2 pair + 1 of L, and row pair `pair` of every column of T
+__device__ __forceinline__ bool p1_unit_ok(const P1Args& a, int pair)
+{
+#if LP_DEBUG
+    const long long ldq = a.ldT / 2;
+    return lp_checked(a.err, pair >= 0 && 2 * pair < a.H && pair < ldq && a.W <= a.ldl &&
+                                 2 * (t_index4(a.ncols - 1, pair, ldq) + 1) <= a.t_elems);
+#else
+    (void)a;
+    (void)pair;
+    return true;
+#endif
+}
+
+// P2 unit: column c of T (all ldT rows), of each spectrum, of each of the
+// launch's U blocks (HoutPad rows) and of the park area
+__device__ __forceinline__ bool p2_column_ok(const P2Args& a, int c, int n, int kw)
+{
+#if LP_DEBUG
+    const bool t_ok = 2 * t_index4(c, 0, a.ldT / 2) + t_row((int)a.ldT - 1) < a.t_elems && a.H <= a.ldT;
+    const bool k_ok = (long long)(c + 1) * a.ldK <= a.k_elems && n <= a.ldK;
+    const bool u_ok = a.HoutPad <= a.ldU &&
+                      (long long)(a.nspec - 1) * a.specU + 2 * u_index4(c, 0, a.ldU / 2) + u_row(a.HoutPad - 1) <
+                          a.u_elems;
+    const bool p_ok = a.park == nullptr || (long long)(c + 1) * n <= a.park_elems;
+    (void)kw;
+    return lp_checked(a.err, c >= 0 && c < a.ncols && t_ok && k_ok && u_ok && p_ok);
+#else
+    (void)a;
+    (void)c;
+    (void)n;
+    (void)kw;
+    return true;
+#endif
+}
+
+// P3 unit: row pair `pair` of every column of U block sidx, rows 2 pair,
+// 2 pair + 1 of out[sidx]
+__device__ __forceinline__ bool p3_unit_ok(const P3Args& a, int pair, int sidx)
+{
+#if LP_DEBUG
+    const long long ldq = a.ldU / 2;
+    return lp_checked(a.err, pair >= 0 && 2 * pair < a.Hout && pair < ldq && a.out[sidx] != nullptr &&
+                                 a.Wout <= a.ldo &&
+                                 (long long)sidx * a.specU + 2 * (u_index4(a.ncols - 1, pair, ldq) + 1) <=
+                                     a.u_elems);
+#else
+    (void)a;
+    (void)pair;
+    (void)sidx;
+    return true;
+#endif
+}
 
 template <int N, class FwdSeq, int TT_ = 0>
 struct Plan {
@@ -323,7 +408,8 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
     float2* sm = smem2 + f * P::SMEM_ELEMS;
     const int pair = a.pair0 + blockIdx.x * F + f;
     const int ra = 2 * pair, rb = ra + 1;
-    const bool va = ra < a.H, vb = rb < a.H;
+    const bool live = pair < a.npairs && p1_unit_ok(a, pair);
+    const bool va = live && ra < a.H, vb = live && rb < a.H;
     const float* La = a.L + (long long)ra * a.ldl;
     const float* Lb = a.L + (long long)rb * a.ldl;
 
@@ -342,7 +428,7 @@ __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
     }
     P::FwdChain::run(v, t, sm, a.tw, [&](float2(&z)[P::EL][P::RL], int tt) {
         to_smem_natural<P, N>(z, tt, sm);
-        if (pair < a.npairs) unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
+        if (live) unpack_rows<N, T>(sm, tt, a.ncols, reinterpret_cast<float4*>(a.T), a.ldT / 2, pair);
     });
 }
 
@@ -408,8 +494,9 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2
     float2* sm = smem2;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
-    const float2* col = t_column(a.T, a.ldT, c);
     constexpr int KW = KREAL ? 1 : 2;  // floats per spectrum value
+    if (!p2_column_ok(a, c, N, KW)) return;  // (whole block: before any barrier)
+    const float2* col = t_column(a.T, a.ldT, c);
     float* kst = reinterpret_cast<float*>(smem2 + (DB ? 2 : 1) * P::SMEM_ELEMS);
     if constexpr (!MULTI && !KST) {
         // the spectrum column is needed after the forward transform: one bulk
@@ -491,7 +578,7 @@ __global__ void __launch_bounds__(P::T * F) p3_rows(const P3Args a)
     const int ra = 2 * pair, rb = ra + 1;
     const float4* Uq = reinterpret_cast<const float4*>(a.U + (long long)sidx * a.specU);
     const long long ldq = a.ldU / 2;
-    const bool live = pair < a.npairs;
+    const bool live = pair < a.npairs && p3_unit_ok(a, pair, sidx);
     const bool vb = rb < a.Hout;
 
     float2 v[P::EI][RI];
@@ -560,7 +647,7 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
     const int Wst = a.Wst;
 
     auto prefetch = [&](int pair) {
-        if (pair >= a.npairs) return;
+        if (pair >= a.npairs || !p1_unit_ok(a, pair)) return;
         const int t = threadIdx.x;
         for (int r = 0; r < 2; ++r) {
             const int row = 2 * pair + r;
@@ -603,7 +690,7 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
     prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {
         const int pair = a.pair0 + blockIdx.x + decltype(I)::value * gridDim.x;
-        if (pair < a.npairs) unit(pair);
+        if (pair < a.npairs && p1_unit_ok(a, pair)) unit(pair);
     });
 }
 
@@ -626,7 +713,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     float* kst = reinterpret_cast<float*>(tst + a.ldT);  // ldK floats or complex
 
     auto prefetch_t = [&](int c) {
-        if (c >= a.ncols) return;
+        if (c >= a.ncols || !p2_column_ok(a, c, N, KW)) return;
         const float4* src = reinterpret_cast<const float4*>(a.T);
         const long long ldq = a.ldT >> 1;
         for (int q = threadIdx.x; q < (int)ldq; q += T) cp_async16(tst + 2 * q, src + t_index4(c, q, ldq));
@@ -634,7 +721,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     };
     auto prefetch_k = [&](int c) {
         if constexpr (!KSTAGE) return;
-        if (c >= a.ncols) return;
+        if (c >= a.ncols || !p2_column_ok(a, c, N, KW)) return;
         const float* src = static_cast<const float*>(a.K[0]) + (long long)c * a.ldK * KW;
         for (int q = threadIdx.x; q < (int)((a.ldK * KW) >> 2); q += T) cp_async16(kst + 4 * q, src + 4 * q);
         cp_async_commit();
@@ -674,7 +761,7 @@ __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
     prefetch_k(blockIdx.x);
     sfor<0, UPB>([&](auto I) {
         const int c = blockIdx.x + decltype(I)::value * gridDim.x;
-        if (c < a.ncols) unit(c);
+        if (c < a.ncols && p2_column_ok(a, c, N, KW)) unit(c);
     });
 }
 
@@ -694,7 +781,7 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
     const long long ldq = a.ldU / 2;
 
     auto prefetch = [&](int pair) {
-        if (pair >= a.npairs) return;
+        if (pair >= a.npairs || !p3_unit_ok(a, pair, sidx)) return;
         for (int k = threadIdx.x; k < a.ncols; k += T) cp_async16(ust + k, Uq + u_index4(k, pair, ldq));
         cp_async_commit();
     };
@@ -727,7 +814,7 @@ __global__ void __launch_bounds__(P::T, MINB) p3_rows_pf(const P3Args a)
     prefetch(a.pair0 + blockIdx.x);
     sfor<0, UPB>([&](auto I) {
         const int pair = a.pair0 + blockIdx.x + decltype(I)::value * gridDim.x;
-        if (pair < a.npairs) unit(pair);
+        if (pair < a.npairs && p3_unit_ok(a, pair, sidx)) unit(pair);
     });
 }
 
@@ -749,7 +836,29 @@ struct P2MArgs {
     int ncols;
     TwChain twf, twi;
     float2* acc;  // the sums of the products, N per column (global memory)
+    int* err;             // device status word (debug builds: bounds checks)
+    long long t_elems;    // float2 elements of each class's T buffer
+    long long k_elems;    // spectrum values of each spectrum
+    long long u_elems;    // float2 elements of U
+    long long acc_elems;  // float2 elements of the sums
 };
+
+// multiclass unit: column c of every class's T, of every spectrum, of U and of the sums
+__device__ __forceinline__ bool p2m_column_ok(const P2MArgs& a, int c, int n)
+{
+#if LP_DEBUG
+    return lp_checked(a.err, c >= 0 && c < a.ncols && a.H <= a.ldT && n <= a.ldK && a.HoutPad <= a.ldU &&
+                                 2 * t_index4(c, 0, a.ldT / 2) + t_row((int)a.ldT - 1) < a.t_elems &&
+                                 (long long)(c + 1) * a.ldK <= a.k_elems &&
+                                 2 * u_index4(c, 0, a.ldU / 2) + u_row(a.HoutPad - 1) < a.u_elems &&
+                                 (long long)(c + 1) * n <= a.acc_elems);
+#else
+    (void)a;
+    (void)c;
+    (void)n;
+    return true;
+#endif
+}
 
 // One class of the Eq. (4) column pass: forward transform of the class's
 // column, product with its spectrum, summed into ACC (natural order; the
@@ -801,6 +910,7 @@ __global__ void __launch_bounds__(P::T) p2_multiclass(const __grid_constant__ P2
     float2* sm = smem2;
     const int c = blockIdx.x;
     const int t = threadIdx.x;
+    if (!p2m_column_ok(a, c, N)) return;  // (whole block: before any barrier)
     // the sums live in global memory (L2-resident while the block runs), so
     // shared memory holds one exchange buffer at every length; every
     // element of ACC is owned by one thread (j + m N/RL), which writes it for

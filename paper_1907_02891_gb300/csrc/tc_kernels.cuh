@@ -530,7 +530,8 @@ __global__ void __launch_bounds__(TcPlan<P, N>::THREADS, TcPlan<P, N>::MINB) p2_
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     TcState st{A.no_mma, sm_u32(Bs), *tslot, sm_u32(mbar), 0u, dead};
 
-    for (int c = blockIdx.x; c < a.ncols; c += gridDim.x) tc_column<P, N, KREAL>(A, c, st);
+    for (int c = blockIdx.x; c < a.ncols; c += gridDim.x)
+        if (p2_column_ok(a, c, N, KREAL ? 1 : 2)) tc_column<P, N, KREAL>(A, c, st);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (t < 32)

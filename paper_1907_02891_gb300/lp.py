@@ -16,7 +16,12 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
+# $LP_DEBUG (not "" or "0") selects the bounds-checked debug build
+# (build.build(debug=True)): every work unit of the passes checks its extents
+# in every buffer first and reports a miss as bit 3 of the device status word
+DEBUG_LIB_PATH = os.path.join(_HERE, "_build", "debug", "liblp.so")
+LIB_PATH = (DEBUG_LIB_PATH if os.environ.get("LP_DEBUG", "") not in ("", "0")
+            else os.path.join(_HERE, "_build", "liblp.so"))
 
 LP_OK, LP_ERR_INVALID, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_TIMEOUT = 0, 1, 2, 3, 4
 LP_ERR_UNSUPPORTED, LP_ERR_BUSY, LP_ERR_DEVICE, LP_ERR_CANCELLED = 5, 6, 7, 8
@@ -293,6 +298,7 @@ PASS_NAMES = ("p1_rows", "p2_cols", "p3_rows")
 LP_TEST_TC_NO_MMA = 1
 LP_TEST_FP_COLLIDE = 2
 LP_TEST_SERVE_FAIL = 4
+LP_TEST_BOUNDS = 8
 
 
 def lp_set_test_hook(ctx: int, hook: int) -> None:
