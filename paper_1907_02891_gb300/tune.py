@@ -162,8 +162,8 @@ def time_variant(lib: str, n: int, reps: int, side: int = 0, psf: int = 0, nspec
 
 
 def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int = 0, psf: int = 0,
-              nspec: int = 1, plans: List[Tuple[int, ...]] = ()) -> dict:
-    base = B.plan_table_entry(n)
+              nspec: int = 1, plans: List[Tuple[int, ...]] = (), packed: bool = False) -> dict:
+    base = dict(B.plan_table_entry(n), packed=packed)
     plans = list(plans) or candidate_plans(n, 2 if quick else 3)
     knobs = []
     for upb, minb, kst in itertools.product((1, 2, 3), (1, 2, 3), (False, True)):
@@ -324,6 +324,8 @@ def main() -> None:
     ap.add_argument("--map-side", type=int, default=0,
                     help="time maps of this side instead of N - PSF + 1, to compare "
                          "padded lengths for one workload")
+    ap.add_argument("--packed", action="store_true",
+                    help="search the knobs with packed FP32x2 arithmetic (the last step still tries both)")
     args = ap.parse_args()
     jobs = args.jobs or (os.cpu_count() or 1)
     logf = open(args.log, "a") if args.log else None
@@ -347,7 +349,8 @@ def main() -> None:
         with open(args.out) as fh:
             table = json.load(fh)
     for n in args.sizes:
-        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side, args.psf, args.nspec, plans)
+        table[str(n)] = tune_size(n, args.quick, jobs, common, log, args.map_side, args.psf, args.nspec, plans,
+                                  args.packed)
         table[str(n)]["tuned_on"] = {"map_side": args.map_side, "psf": args.psf, "nspec": args.nspec}
         with open(args.out, "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
