@@ -70,9 +70,10 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-log", default=None,
                     help="--mode serve: append one JSON line per request to this file")
-    ap.add_argument("--forms", default="batched,split_bf16,tiled,graph,serve",
+    ap.add_argument("--forms", default="batched,split_bf16,same_pad,tiled,graph,serve",
                     help="forms measured beside the headline map (comma list; empty: none): "
                          "batched (8192^2, 16 PSFs), split_bf16 (16384^2, 801^2 PSF), "
+                         "same_pad (4096^2 map in one tile at the SAME crop's padding), "
                          "tiled (17800 x 21000, 801^2 PSF, overlap-save tiles), "
                          "graph (loops of small maps as one CUDA-graph replay), "
                          "serve (Poisson requests at 130%% and at 70%% load)")
@@ -622,6 +623,55 @@ def _form_tiled(lp, args, wl, flush, stream, dev):
         lp.lp_destroy(ctx)
 
 
+def _form_same_pad(lp, args, wl, flush, stream, dev):
+    """The SAME crop at its own padding: a map that one transform holds,
+    through lp_map_tiled in one tile at the padding lp_tiled_pad picks
+    (h + (hk - 1) / 2 instead of lp_map's h + hk - 1), against lp_map on the
+    same map; Mpix/s and the error against the oracle."""
+    import torch
+    H, W = wl.H, wl.W
+    L_host = wl.radiance()
+    (K,) = wl.psfs()
+    hk = K.shape[0]
+    ctx = lp.lp_create(dev.index or 0)
+    try:
+        L = torch.from_numpy(L_host).to(dev)
+        Kd = torch.from_numpy(K).to(dev)
+        ny, nx = lp.lp_tiled_pad(H, W, hk, hk)
+        spec = lp.lp_kernel_spectrum(ctx, Kd, pad_ny=ny, pad_nx=nx)
+        out = torch.empty((H, W), dtype=torch.float32, device=dev)
+        steps, warm = max(3, min(args.steps, 20)), max(3, min(args.warmup, 5))
+        ev = []
+        for k in range(warm + steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lp.lp_map_tiled(ctx, L, [spec], [out])
+            b.record(stream)
+            if k >= warm:
+                ev.append((a, b))
+        torch.cuda.synchronize()
+        lp.lp_sync_status(ctx)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        err = cpu_baseline_leg_error(L_host, [K], [out], wl.seed + 400)
+        lp.lp_spectrum_release(ctx, spec)
+        nyp, nxp = lp.lp_supported_size(H + hk - 1), lp.lp_supported_size(W + hk - 1)
+        sp = lp.lp_kernel_spectrum(ctx, Kd, pad_ny=nyp, pad_nx=nxp)
+        pms = statistics.mean(_time_maps(lp, ctx, L, [sp], [out], lp.LP_PREC_FP32, steps, warm, flush, stream))
+        lp.lp_spectrum_release(ctx, sp)
+        lp.lp_sync_status(ctx)
+        return {"workload": wl.name, "map": f"{H}x{W}", "psf": f"{hk}x{hk}", "padded": f"{ny}x{nx}",
+                "tiles": 1 if (H <= ny - (hk - 1) // 2 and W <= nx - (hk - 1) // 2) else None,
+                "precision": "fp32", "mpix_s": H * W / (ms / 1e3) / 1e6, "ms_per_step": ms, "steps": steps,
+                "max_norm_err": err, "tolerance": 1e-5,
+                "plain_fp32": {"mpix_s": H * W / (pms / 1e3) / 1e6, "ms_per_step": pms, "padded": f"{nyp}x{nxp}",
+                               "what": "lp_map, padded to h + hk - 1 (Sec. 2.5)"},
+                "speedup_vs_plain_fp32": pms / ms,
+                "what": "lp_map_tiled in one tile padded to h + (hk - 1) / 2, enough for the SAME crop"}
+    finally:
+        lp.lp_destroy(ctx)
+
+
 def _graph_case(lp, flush, dev, side, psf, n_maps, steps, seed):
     """n_maps maps of side^2 with one psf^2 PSF, each its own input and
     output: direct lp_map_noalloc calls against one replay of the same calls
@@ -845,6 +895,8 @@ def run_ours(args, rank, world, local_rank):
                                             flush, stream, dev)
         if "graph" in want:
             forms["graph"] = _form_graph(lp, args, flush, stream, dev)
+        if "same_pad" in want:
+            forms["same_pad"] = _form_same_pad(lp, args, synth.WORKLOADS["map4096_psf541"], flush, stream, dev)
         if "tiled" in want:
             forms["tiled"] = _form_tiled(lp, args, synth.WORKLOADS["map17800x21000_psf801"], flush, stream, dev)
         if "serve" in want:

@@ -305,7 +305,10 @@ lp_status lp_set_test_hook(lp_ctx* ctx, int hook);
  * Maps larger than the padded size (overlap-save tiling; Sec. 4 computes
  * extended regions band by band, here the pieces share one grid).  The SAME-mode result of
  * lp_map for an h x w map of any size, computed in tiles of
- * (Ny - hk + 1) x (Nx - wk + 1) output pixels: each tile convolves the input
+ * (Ny - hk + 1) x (Nx - wk + 1) output pixels, or in one tile along a
+ * dimension where h <= Ny - (hk - 1) / 2 (w <= Nx - (wk - 1) / 2: the SAME
+ * crop needs no more padding than that, less than lp_map's h + hk - 1):
+ * each tile convolves the input
  * window that covers it plus the PSF's reach ((hk - 1) / 2 rows,
  * (wk - 1) / 2 columns, clipped to the map) in one P1 / P2 / P3 sequence,
  * which is exact for the tile's pixels (no wrap-around reaches them), and
@@ -323,9 +326,10 @@ lp_status lp_map_tiled(lp_ctx* ctx, const float* L, int h, int w, int ldl,
 /*
  * Padded size for lp_map_tiled (host only, no device needed): per dimension
  * the supported length N >= hk (>= wk) that minimises the points transformed
- * over all tiles, ceil(h / (N - hk + 1)) * N (ties: fewer tiles); for
- * LP_PREC_SPLIT_BF16 the column length has the tensor-core pass.  A map
- * that one transform holds whole usually gets the lp_map padding (one tile).
+ * over all tiles, tiles * N, with the tiles lp_map_tiled cuts (one where
+ * h <= N - (hk - 1) / 2, else ceil(h / (N - hk + 1))); ties: fewer tiles.
+ * For LP_PREC_SPLIT_BF16 the column length has the tensor-core pass.  A map
+ * one transform holds usually gets one tile at the SAME crop's padding.
  * Errors: LP_ERR_INVALID (empty map, even or non-positive PSF sides, NULL
  * outputs), LP_ERR_UNSUPPORTED (precision, or no length holds the PSF);
  * the outputs are -1 on error.

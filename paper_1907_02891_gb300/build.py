@@ -46,11 +46,12 @@ SMEM_LIMIT = 227 * 1024
 
 # Supported transform lengths.  Every length is 7-smooth; the list covers
 # the workload sizes (360, 480, 720, 1260, 2250, 4320, 4704, 8400, 8820,
-# 17280), powers of two, and a ladder in between.
+# 17280; 4608 = 4096 + 512 for the 4096^2 map's SAME crop with a 541^2 PSF
+# in one tile), powers of two, and a ladder in between.
 SIZES = (
     45, 64, 96, 100, 120, 128, 160, 192, 210, 240, 256, 288, 320, 360, 384, 420, 480, 512,
     560, 640, 720, 768, 840, 960, 1024, 1120, 1260, 1344, 1536, 1680, 1792, 2048, 2250, 2520,
-    2688, 3072, 3360, 3584, 4096, 4320, 4704, 4800, 4860, 5040, 5120, 5376, 6144, 6720, 7168,
+    2688, 3072, 3360, 3584, 4096, 4320, 4608, 4704, 4800, 4860, 5040, 5120, 5376, 6144, 6720, 7168,
     8192, 8400, 8640, 8820, 9000, 9216,
     10080, 10752, 12288, 13440, 15360, 16384, 17280,
 )
@@ -433,13 +434,20 @@ def build(jobs: int = 0, verbose: bool = False, debug: bool = False, sizes: Sequ
     jobs = jobs or max(1, os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, deps, debug), srcs))
-    if (not os.path.exists(lib)) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+    # relink when an object is newer or the set of objects differs (a debug
+    # build of another subset of lengths)
+    manifest = lib + ".objs"
+    listed = open(manifest).read() if os.path.exists(manifest) else ""
+    if (not os.path.exists(lib) or listed != "\n".join(objs) or
+            os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs)):
         tmp = lib + f".tmp{os.getpid()}"
         cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, lib)
+        with open(manifest, "w") as fh:
+            fh.write("\n".join(objs))
     if verbose:
         print(lib)
     return lib

@@ -94,18 +94,20 @@ static int tc_supported_size(int n)
 }
 
 // Padded length of one dimension for the tiled map: the supported length
-// N >= k that minimises the transformed points of that dimension,
-// ceil(n / (N - k + 1)) * N (ties: fewer tiles); with tc, only lengths that
-// have the tensor-core column pass.
+// N >= k that minimises the transformed points of that dimension, tiles * N
+// with one tile where n <= N - (k - 1) / 2, else ceil(n / (N - k + 1))
+// (ties: fewer tiles); with tc, only lengths that have the tensor-core
+// column pass.
 static int tile_length(int n, int k, bool tc)
 {
     long long best_cost = -1;
     int best = -1, best_tiles = 0;
+    const int c = (k - 1) / 2;
     for (int i = 0; i < kNumSizes; ++i) {
         const int N = kAllSizes[i]->N;
         if (N < k || (tc && kAllSizes[i]->tc_smem == 0)) continue;
         const int t = N - k + 1;
-        const int tiles = (n + t - 1) / t;
+        const int tiles = n <= N - c ? 1 : (n + t - 1) / t;   // as lp_map_tiled cuts them
         const long long cost = (long long)tiles * N;
         if (best < 0 || cost < best_cost || (cost == best_cost && tiles < best_tiles)) {
             best = N;
@@ -1173,7 +1175,10 @@ extern "C" lp_status lp_map(lp_ctx* ctx, const float* L, int h, int w, int ldl,
 // the window ends at most th + cy rows after the tile's start, so a kept
 // output row o and an input row i of the window satisfy |o - i| <= th + cy
 // - 1, and o - i +- Ny never falls within the PSF's support [-cy, cy].
-// Hence th = Ny - (hk - 1) (hk = 2 cy + 1), and tw = Nx - (wk - 1) alike.  Each tile is one P1 / P2 / P3 sequence on the
+// Hence th = Ny - (hk - 1) (hk = 2 cy + 1), and tw = Nx - (wk - 1) alike.
+// A dimension the map covers in one tile has no margin beyond the map:
+// there |o - i| <= h - 1, so h <= Ny - cy suffices (the SAME crop's own
+// padding rule, tighter than h + hk - 1).  Each tile is one P1 / P2 / P3 sequence on the
 // window (row and column offsets of the crop r0 = a - window start,
 // c0 alike), writing its tile of out[] in place; tiles run in stream order
 // and share one workspace.
@@ -1187,7 +1192,9 @@ extern "C" lp_status lp_map_tiled(lp_ctx* ctx, const float* L, int h, int w, int
     const lp_spectrum* s0 = spectra[0];
     const int ny = s0->ny, nx = s0->nx, hk = s0->hk, wk = s0->wk;
     const int cy = (hk - 1) / 2, cx = (wk - 1) / 2;
-    const int th = ny - (hk - 1), tw = nx - (wk - 1);
+    // one tile where the whole dimension fits (h <= Ny - cy), else tiles of
+    // Ny - (hk - 1)
+    const int th = h <= ny - cy ? h : ny - (hk - 1), tw = w <= nx - cx ? w : nx - (wk - 1);
     if (th < 1 || tw < 1)
         return lp_fail(LP_ERR_INVALID, "lp_map_tiled: padded size %d x %d leaves no tile for a %d x %d PSF", ny, nx,
                        hk, wk);

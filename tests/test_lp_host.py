@@ -87,9 +87,10 @@ def test_no_gpu_errors_are_reported_not_raised(lib):
 
 def test_tiled_pad_minimises_transformed_points(lib):
     """lp_tiled_pad against a brute-force search of the size table: per
-    dimension the length N >= k with the fewest points ceil(n / (N - k + 1))
-    N over all tiles (ties: fewer tiles); maps one transform holds keep the
-    lp_map padding."""
+    dimension the length N >= k with the fewest points tiles * N over all
+    tiles, one tile where n <= N - (k - 1) / 2, else ceil(n / (N - k + 1))
+    (ties: fewer tiles); maps one transform holds get one tile at the SAME
+    crop's padding."""
     from paper_1907_02891_gb300 import lp
     sizes = lp.supported_sizes()
 
@@ -98,7 +99,7 @@ def test_tiled_pad_minimises_transformed_points(lib):
         for N in sizes:
             if N < k or (split and not lp.lp_split_supported(N)):
                 continue
-            tiles = -(-n // (N - k + 1))
+            tiles = 1 if n <= N - (k - 1) // 2 else -(-n // (N - k + 1))
             key = (tiles * N, tiles)
             if best is None or key < best[0]:
                 best = (key, N)
@@ -108,11 +109,26 @@ def test_tiled_pad_minimises_transformed_points(lib):
                          (1, 1, 1, 1), (5000, 40000, 541, 1), (65, 65, 63, 63)):
         assert lp.lp_tiled_pad(h, w, hk, wk) == (brute(h, hk), brute(w, wk)), (h, w, hk, wk)
         assert lp.lp_tiled_pad(h, w, hk, wk, lp.LP_PREC_SPLIT_BF16)[0] == brute(h, hk, True)
-    for side, k in ((256, 101), (4096, 541), (8192, 601), (16384, 801)):
-        n = lp.lp_supported_size(side + k - 1)
+    for side, k, n in ((256, 101, 320), (4096, 541, 4608), (8192, 601, 8640), (16384, 801, 17280)):
+        assert n == lp.lp_supported_size(side + (k - 1) // 2)
         assert lp.lp_tiled_pad(side, side, k, k) == (n, n)
     for bad in ((0, 10, 3, 3), (10, 10, 4, 3), (10, 10, 3, -1)):
         with pytest.raises(lp.LpError):
             lp.lp_tiled_pad(*bad)
     with pytest.raises(lp.LpError):   # no supported length holds the PSF
         lp.lp_tiled_pad(10, 10, 2 * max(sizes) + 1, 3)
+
+
+def test_debug_build_compiles_and_exports(lib):
+    """The bounds-checked debug library (one length here) builds with the
+    same toolchain and exports the same entry points."""
+    import ctypes
+    from paper_1907_02891_gb300 import build
+    path = build.build(debug=True, sizes=(96,))
+    assert path == build.DEBUG_LIB and os.path.exists(path)
+    dl = ctypes.CDLL(path)
+    for name in _declared_symbols():
+        assert hasattr(dl, name), name
+    dl.lp_num_supported_sizes.restype = ctypes.c_int
+    dl.lp_supported_size_at.restype = ctypes.c_int
+    assert dl.lp_num_supported_sizes() == 1 and dl.lp_supported_size_at(0) == 96

@@ -70,8 +70,10 @@ def test_tiles_cover_the_map_exactly(ctx):
 
 
 @pytest.mark.parametrize("shape,psf,pad", [
-    ((66, 66), 31, (96, 96)),      # exactly one tile
-    ((67, 133), 31, (96, 96)),     # one row and one column past a tile edge
+    ((66, 66), 31, (96, 96)),      # one tile (h <= Ny - cy = 81)
+    ((81, 81), 31, (96, 96)),      # one tile at the SAME crop's padding limit, Ny = h + cy
+    ((82, 133), 31, (96, 96)),     # one row / 52 columns past that: tiles of 66
+    ((133, 67), 31, (96, 96)),     # the transpose
     ((1, 1), 31, (96, 96)),        # a single pixel
     ((40, 25), 31, (96, 96)),      # smaller than one tile
     ((257, 190), 45, (100, 64)),   # unequal paddings, tiles of 56 x 20
@@ -84,6 +86,26 @@ def test_ragged_and_degenerate_tilings(ctx, shape, psf, pad):
     (B,) = tiled(ctx, L, [K], pad)
     assert np.isfinite(B).all()
     assert err(B, oracle.conv_same(L, K)) <= TOL_FP32
+
+
+def test_one_tile_at_the_same_crops_padding(ctx):
+    """A 4096^2 map with the 541^2 PSF in one 4608^2 transform (4096 + 270
+    <= 4608 < 4096 + 540, the padding lp_map needs): sampled against the
+    oracle, the pixels of the first and last rows and columns (where the
+    wrap-around would land first) included."""
+    wl = synth.WORKLOADS["map4096_psf541"]
+    L, (K,) = wl.radiance(), wl.psfs()
+    assert lp.lp_tiled_pad(4096, 4096, 541, 541) == (4608, 4608)
+    (B,) = tiled(ctx, L, [K], (4608, 4608))
+    H, W = B.shape
+    g = np.random.default_rng(1907_02891 + 66)
+    ii, jj = synth.sample_pixels(H, W, 4096, 1907_02891 + 67)
+    flat = np.argpartition(B.ravel(), -64)[-64:]
+    edge = np.array([0, 1, H - 2, H - 1])
+    ii = np.concatenate([ii, flat // W, np.repeat(edge, 64), g.integers(0, H, 256)])
+    jj = np.concatenate([jj, flat % W, g.integers(0, W, 256), np.repeat(edge, 64)])
+    ref = oracle.conv_points_same(L, K, ii, jj)
+    assert err(B[ii, jj], ref) <= TOL_FP32
 
 
 def test_tiled_split_precision(ctx):
