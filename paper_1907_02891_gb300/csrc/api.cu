@@ -467,7 +467,8 @@ extern "C" void lp_destroy(lp_ctx* ctx)
     }
     for (auto ev : ctx->tim_pool) cudaEventDestroy(ev);
     for (auto ev : ctx->hs_events) cudaEventDestroy(ev);
-    if (ctx->hs_lfree) cudaEventDestroy(ctx->hs_lfree);
+    for (auto ev : ctx->hs_lfree)
+        if (ev) cudaEventDestroy(ev);
     for (auto ev : ctx->hs_ofree)
         if (ev) cudaEventDestroy(ev);
     if (ctx->hs_in) cudaStreamDestroy(ctx->hs_in);
@@ -1272,7 +1273,7 @@ static lp_status host_streams(lp_ctx* ctx)
         CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->hs_events.push_back(e);
     }
-    CUDA_TRY(cudaEventCreateWithFlags(&ctx->hs_lfree, cudaEventDisableTiming));
+    for (auto& ev : ctx->hs_lfree) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     return LP_OK;
 }
 
@@ -1293,12 +1294,13 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     const PlanRec *py, *px;
     if ((st = lp_get_plan(ctx, s0->ny, &py)) != LP_OK) return st;
     if ((st = lp_get_plan(ctx, s0->nx, &px)) != LP_OK) return st;
-    // staging: L (h x w, packed), then two sets of n outputs (Hout x Wout,
-    // packed) that alternate between calls
+    // staging: two maps L (h x w, packed), then two sets of n outputs
+    // (Hout x Wout, packed); both alternate between calls, so that a map's
+    // upload need not wait for the previous map's row pass
     const size_t lbytes = 4ull * (size_t)h * w;
     const size_t obytes = 4ull * (size_t)d.Hout * d.Wout;
     const size_t lb = (lbytes + 255) / 256 * 256, ob = (obytes + 255) / 256 * 256;
-    const size_t need = lb + 2ull * (size_t)n * ob;
+    const size_t need = 2ull * lb + 2ull * (size_t)n * ob;
     std::lock_guard<std::mutex> host_lock(ctx->host_mu);  // one host map enqueued at a time per context
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
@@ -1316,17 +1318,17 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
             if (st != LP_OK) return st;
             ctx->staging = p;
             ctx->staging_bytes = need;
-            ctx->hs_lfree_valid = false;
+            ctx->hs_lfree_valid[0] = ctx->hs_lfree_valid[1] = false;
             ctx->hs_ofree_valid[0] = ctx->hs_ofree_valid[1] = false;
         }
     }
     if ((st = host_streams(ctx)) != LP_OK) return st;
     cudaStream_t c = ctx->hs_comp;  // the passes of host maps run here, with their own workspace
-    const int obuf = ctx->hs_obuf;
+    const int obuf = ctx->hs_obuf, lbuf = ctx->hs_lbuf;
     char* base = static_cast<char*>(ctx->staging);
-    float* dL = reinterpret_cast<float*>(base);
+    float* dL = reinterpret_cast<float*>(base + (size_t)lbuf * lb);
     std::vector<float*> dout(n);
-    for (int k = 0; k < n; ++k) dout[k] = reinterpret_cast<float*>(base + lb + ((size_t)obuf * n + k) * ob);
+    for (int k = 0; k < n; ++k) dout[k] = reinterpret_cast<float*>(base + 2 * lb + ((size_t)obuf * n + k) * ob);
     void* ws = nullptr;
     st = lp_get_workspace(ctx, c, lp_map_workspace_bytes(h, w, s0->ny, s0->nx, s0->hk, s0->wk, n, mode), &ws);
     if (st != LP_OK) return st;
@@ -1338,11 +1340,11 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     cudaEvent_t ev_start = ev[0], ev_end = ev[1];
     cudaEvent_t* ev_in = ev + 2;                 // kHostBands
     cudaEvent_t* ev_out = ev + 2 + kHostBands;   // kHostBands
-    cudaEvent_t ev_lfree = ctx->hs_lfree;
+    cudaEvent_t ev_lfree = ctx->hs_lfree[lbuf];
 
-    // Ordering.  The upload waits until the previous host map's row pass has
-    // read the staging map (the first time: for the caller's earlier work on
-    // the stream).  The passes wait only for their input bands, the spectra's
+    // Ordering.  The upload waits until the row pass of the host map two back
+    // (the last one that used this input staging buffer) has read it (the
+    // first time: for the caller's earlier work on the stream).  The passes wait only for their input bands, the spectra's
     // builds, and -- before writing output staging buffer b -- the download
     // of the call two back that used b; so a map's passes overlap the
     // previous map's download.  The download waits for the caller's earlier
@@ -1350,7 +1352,7 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
     // waits for the download, so the stream reaches the end of this call only
     // with every output in host memory.
     CUDA_TRY(cudaEventRecord(ev_start, s));
-    if (ctx->hs_lfree_valid) CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_lfree, 0));
+    if (ctx->hs_lfree_valid[lbuf]) CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_lfree, 0));
     else CUDA_TRY(cudaStreamWaitEvent(ctx->hs_in, ev_start, 0));
     CUDA_TRY(cudaStreamWaitEvent(ctx->hs_out, ev_start, 0));
     for (int k = 0; k < n; ++k) CUDA_TRY(cudaStreamWaitEvent(c, spectra[k]->ready, 0));
@@ -1367,8 +1369,9 @@ extern "C" lp_status lp_map_host(lp_ctx* ctx, const float* L_host, int h, int w,
         CUDA_TRY(cudaStreamWaitEvent(c, ev_in[b], 0));
         if ((st = launch_rows_forward(ctx, px, dL, h, w, w, d, T, q0, q1, c)) != LP_OK) return st;
     }
-    CUDA_TRY(cudaEventRecord(ev_lfree, c));  // the staging map may be overwritten after this
-    ctx->hs_lfree_valid = true;
+    CUDA_TRY(cudaEventRecord(ev_lfree, c));  // this input staging map may be overwritten after this
+    ctx->hs_lfree_valid[lbuf] = true;
+    ctx->hs_lbuf = lbuf ^ 1;
     const int opairs = (int)(d.ldU / 2);
     const int nb_out = host_bands(obytes * (size_t)n, opairs);
     for (int cb = 0; cb < n; cb += kMaxSpectraPerLaunch) {

@@ -113,8 +113,9 @@ struct lp_ctx {
     std::mutex host_mu;
     cudaStream_t hs_in = nullptr, hs_out = nullptr, hs_comp = nullptr;
     std::vector<cudaEvent_t> hs_events;
-    cudaEvent_t hs_lfree = nullptr;  // previous host map's row pass done with the staging map
-    bool hs_lfree_valid = false;
+    cudaEvent_t hs_lfree[2] = {nullptr, nullptr};  // row pass done with input staging b
+    bool hs_lfree_valid[2] = {false, false};
+    int hs_lbuf = 0;  // input staging buffer of the next host map
     cudaEvent_t hs_ofree[2] = {nullptr, nullptr};  // download from output staging b done
     bool hs_ofree_valid[2] = {false, false};
     int hs_obuf = 0;  // output staging buffer of the next host map

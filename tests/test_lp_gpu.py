@@ -241,8 +241,9 @@ def test_host_entry_point_banded_ragged_full_mode(ctx):
 
 
 def test_host_entry_point_back_to_back_calls(ctx):
-    """Consecutive host maps overlap (a map's passes with the previous map's
-    download, output staging alternating between two buffers): five calls
+    """Consecutive host maps overlap (a map's upload with the previous map's
+    passes, its passes with the previous map's download; input and output
+    staging alternating between two buffers each): five calls
     with different maps and two spectra, one sync at the end, every output
     bitwise equal to the device path's."""
     g = np.random.default_rng(17)
