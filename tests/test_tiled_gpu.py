@@ -108,6 +108,18 @@ def test_one_tile_at_the_same_crops_padding(ctx):
     assert err(B[ii, jj], ref) <= TOL_FP32
 
 
+def test_more_spectra_than_one_launch_takes_in_every_tile(ctx):
+    """33 PSFs (one more than a column launch takes) over a 4 x 3 tile grid:
+    every tile runs its spectra in two chunks; the first, the 32nd and the
+    33rd output against the oracle, all of them finite."""
+    L = synth.radiance_map(200, 150, 12, 1907_02891 + 68, lit_fraction=0.05)
+    Ks = [synth.psf_power_exp(15, 0.742, 0.1, 1.0 + 0.03 * i, 40.0 + 5.0 * i) for i in range(33)]
+    Bs = tiled(ctx, L, Ks, (64, 64))
+    assert all(np.isfinite(B).all() for B in Bs)
+    for i in (0, 31, 32):
+        assert err(Bs[i], oracle.conv_same(L, Ks[i])) <= TOL_FP32, i
+
+
 def test_tiled_split_precision(ctx):
     L = synth.radiance_map(300, 300, 20, 1907_02891 + 62, lit_fraction=0.05)
     K = synth.psf_power_exp(41, 0.742, 0.1, 1.25, 80.0)
