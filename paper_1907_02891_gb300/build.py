@@ -152,7 +152,8 @@ def plan_table() -> Dict[int, dict]:
                      upb=list(t["upb"]), minb=list(t["minb"]), kstage=bool(t["kstage"]),
                      tt=int(t.get("tt", 0)), pf=list(t.get("pf", [1, 1, 1])),
                      db=list(t.get("db", [0, 0, 0])), batch=bool(t.get("batch", True)),
-                     kst2=bool(t.get("kst2", False)), packed=bool(t.get("packed", False)))
+                     kst2=bool(t.get("kst2", False)), packed=bool(t.get("packed", False)),
+                     late=list(t.get("late", [0, 0, 0])))
             if e["tt"]:
                 e["threads"] = e["tt"]
         table[n] = e
@@ -180,6 +181,9 @@ constexpr int kMINB1 = {minb1}, kMINB2 = {minb2}, kMINB3 = {minb3};
 constexpr bool kKSTAGE = {kstage};
 constexpr bool kPF1 = {pf1}, kPF2 = {pf2}, kPF3 = {pf3};   // prefetching form allowed per pass
 constexpr bool kDB1 = {db1}, kDB2 = {db2}, kDB3 = {db3};   // double-buffered exchange per pass
+// forward row pass / one-spectrum column pass: the next kernel launches as
+// this one's blocks exit instead of once they have all started
+constexpr bool kLATE1 = {late1}, kLATE2 = {late2};
 // several spectra: the batched column kernel (forward column parked in global
 // memory, one product + inverse per spectrum) or one single-spectrum pass per
 // spectrum (forward transform repeated)
@@ -214,9 +218,9 @@ inline int persistent_grid(int units, int upb) {{ return (units + upb - 1) / upb
 cudaError_t set_attrs()
 {{
     cudaError_t e;
-    if ((e = attr(p1_rows<P, kN, kF1>, kF1 * kSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true)>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
-    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
+    if ((e = attr(p1_rows<P, kN, kF1, kLATE1>, kF1 * kSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true), false, kLATE2>, kX2 * kSmem + kKst(true))) != cudaSuccess) return e;
+    if ((e = attr(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false), false, kLATE2>, kX2 * kSmem + kKst(false))) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, true, true, 1, false, false, kParkG>, kSmemM)) != cudaSuccess) return e;
     if ((e = attr(p2_cols<P, kN, false, true, 1, false, false, kParkG>, kSmemM)) != cudaSuccess) return e;
     if ((e = attr(p2_multiclass<P, kN, true>, kSmem)) != cudaSuccess) return e;
@@ -226,9 +230,9 @@ cudaError_t set_attrs()
         if ((e = attr(p2_cols_tc<P, kN, true>, kTcSmem)) != cudaSuccess) return e;
         if ((e = attr(p2_cols_tc<P, kN, false>, kTcSmem)) != cudaSuccess) return e;
     }}
-    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
-    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1, kLATE1>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2, kLATE2>, (int)kMaxSmem)) != cudaSuccess) return e;
+    if ((e = attr(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2, kLATE2>, (int)kMaxSmem)) != cudaSuccess) return e;
     return attr(p3_rows_pf<P, kN, kUPB3, kMINB3, kDB3>, (int)kMaxSmem);
 }}
 
@@ -236,9 +240,9 @@ cudaError_t p1(const P1Args& a, cudaStream_t s)
 {{
     const long long sm = kX1 * kSmem + p1_stage_bytes(a.Wst);
     if (kPF1 && sm <= kMaxSmem)
-        return launch_pdl(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1>, dim3(persistent_grid(a.npairs - a.pair0, kUPB1)),
+        return launch_pdl(p1_rows_pf<P, kN, kUPB1, kMINB1, kDB1, kLATE1>, dim3(persistent_grid(a.npairs - a.pair0, kUPB1)),
                           dim3(P::T), sm, s, a);
-    return launch_pdl(p1_rows<P, kN, kF1>, dim3((a.npairs - a.pair0 + kF1 - 1) / kF1), dim3(P::T * kF1),
+    return launch_pdl(p1_rows<P, kN, kF1, kLATE1>, dim3((a.npairs - a.pair0 + kF1 - 1) / kF1), dim3(P::T * kF1),
                       kF1 * kSmem, s, a);
 }}
 
@@ -249,11 +253,11 @@ cudaError_t p2(const P2Args& a, bool kreal, cudaStream_t s)
     if (!multi) {{
         const dim3 gpf(persistent_grid(a.ncols, kUPB2));
         if (kPF2 && sm <= kMaxSmem)
-            return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a)
-                         : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2>, gpf, dim3(P::T), sm, s, a);
-        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true)>, dim3(a.ncols), dim3(P::T),
+            return kreal ? launch_pdl(p2_cols_pf<P, kN, true, kUPB2, kMINB2, kKSTAGE, kDB2, kLATE2>, gpf, dim3(P::T), sm, s, a)
+                         : launch_pdl(p2_cols_pf<P, kN, false, kUPB2, kMINB2, kKSTAGE, kDB2, kLATE2>, gpf, dim3(P::T), sm, s, a);
+        return kreal ? launch_pdl(p2_cols<P, kN, true, false, kMINB2, kDB2, kKstOk(true), false, kLATE2>, dim3(a.ncols), dim3(P::T),
                                   kX2 * kSmem + kKst(true), s, a)
-                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false)>, dim3(a.ncols), dim3(P::T),
+                     : launch_pdl(p2_cols<P, kN, false, false, kMINB2, kDB2, kKstOk(false), false, kLATE2>, dim3(a.ncols), dim3(P::T),
                                   kX2 * kSmem + kKst(false), s, a);
     }}
     if (kBatch && (!kParkG || a.park)) {{
@@ -384,6 +388,7 @@ def generate(sizes: Sequence[int] = ()) -> List[str]:
                                db1=_b(p["db"][0]), db2=_b(p["db"][1]), db3=_b(p["db"][2]),
                                batch=_b(p.get("batch", True)),
                                kst2=_b(p.get("kst2", False)), packed=int(bool(p.get("packed", False))),
+                               late1=_b(p.get("late", [0, 0, 0])[0]), late2=_b(p.get("late", [0, 0, 0])[1]),
                                rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
         path = os.path.join(gen, f"size_{n}.cu")
         _write_if_changed(path, text)

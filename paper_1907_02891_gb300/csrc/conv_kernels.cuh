@@ -256,10 +256,15 @@ struct Plan {
 // stream has completed with its memory visible -- so no pass touches global
 // memory before its predecessor is done, while the launch latency of each
 // pass overlaps the tail of the one before.  Without the attribute (or after
-// a non-kernel operation) the wait returns at once.
+// a non-kernel operation) the wait returns at once.  With LATE the block
+// does not trigger, so the next kernel launches only as this grid's blocks
+// exit: measured faster for the forward row pass at three resident blocks
+// per SM (the next pass's early blocks otherwise share its last wave's SMs),
+// a plan knob per pass.
+template <bool LATE = false>
 __device__ __forceinline__ void pdl_begin()
 {
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    if constexpr (!LATE) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
@@ -396,10 +401,10 @@ __device__ __forceinline__ void store_rows(const float2 (&o)[P::EJ][P::R0], int 
 // ---------------------------------------------------------------------------
 // P1: row R2C of two packed rows per transform, F transforms per block.
 // ---------------------------------------------------------------------------
-template <class P, int N, int F>
+template <class P, int N, int F, bool LATE = false>
 __global__ void __launch_bounds__(P::T * F) p1_rows(const P1Args a)
 {
-    pdl_begin();
+    pdl_begin<LATE>();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -480,10 +485,10 @@ __device__ __forceinline__ void cp_async_wait_all();
 // (a.park) instead of shared memory, for lengths whose exchange buffer and
 // parked column do not fit shared memory together.
 template <class P, int N, bool KREAL, bool MULTI, int MINB = 1, bool DB = false, bool KST = false,
-          bool PARKG = false>
+          bool PARKG = false, bool LATE = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols(const __grid_constant__ P2Args a)
 {
-    pdl_begin();
+    pdl_begin<LATE>();
     static_assert(!(DB && MULTI), "the batched column pass is single-buffered");
     static_assert(!(KST && MULTI), "spectrum staging is for one spectrum");
     using Fwd = typename std::conditional<DB, typename P::FwdChainDB, typename P::FwdChain>::type;
@@ -633,10 +638,10 @@ __host__ __device__ constexpr long long p2_stage_bytes(long long ldT, long long 
 }
 __host__ __device__ constexpr long long p3_stage_bytes(int ncols) { return 16ll * ncols; }
 
-template <class P, int N, int UPB, int MINB, bool DB = false>
+template <class P, int N, int UPB, int MINB, bool DB = false, bool LATE = false>
 __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 {
-    pdl_begin();
+    pdl_begin<LATE>();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
@@ -696,10 +701,10 @@ __global__ void __launch_bounds__(P::T, MINB) p1_rows_pf(const P1Args a)
 
 // single spectrum; T column staged, K^ column staged when KSTAGE (else read
 // directly at the product)
-template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE, bool DB = false>
+template <class P, int N, bool KREAL, int UPB, int MINB, bool KSTAGE, bool DB = false, bool LATE = false>
 __global__ void __launch_bounds__(P::T, MINB) p2_cols_pf(const P2Args a)
 {
-    pdl_begin();
+    pdl_begin<LATE>();
     extern __shared__ float2 smem2[];
     constexpr int T = P::T;
     constexpr int R0 = P::R0, NB0 = N / R0;
