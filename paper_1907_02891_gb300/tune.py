@@ -95,7 +95,7 @@ def _variant_lib(n: int, plan: dict, common: List[str]) -> str:
                              db1=B._b(plan["db"][0]), db2=B._b(plan["db"][1]), db3=B._b(plan["db"][2]),
                              batch=B._b(plan.get("batch", True)),
                              kst2=B._b(plan.get("kst2", False)), packed=int(bool(plan.get("packed", False))),
-                             late1=B._b(plan.get("late", [0, 0, 0])[0]), late2=B._b(plan.get("late", [0, 0, 0])[1]),
+                             late1=B._b(plan.get("late", B.DEFAULT_LATE)[0]), late2=B._b(plan.get("late", B.DEFAULT_LATE)[1]),
                              rad6=", ".join(map(str, r + [0] * (6 - len(r)))))
     src = os.path.join(d, f"size_{n}.cu")
     with open(src, "w") as fh:
