@@ -134,7 +134,7 @@ def kernel_source_sha(extra=(), lengths=()):
     for n in sorted(set(lengths)):
         e = tuned.get(str(n))
         if isinstance(e, dict):  # knobs only: notes and tuning metadata change no kernel
-            e = {k: v for k, v in e.items() if k not in ("note", "tuned_on", "tuned_total_us")}
+            e = {k: v for k, v in e.items() if k not in ("note", "tuned_on", "tuned_total_us", "tuned_map_us")}
         h.update(json.dumps(e, sort_keys=True).encode())
     return h.hexdigest()[:16]
 

@@ -145,6 +145,18 @@ mapf = lp.lp_map if min(h, w) + hk - 1 <= n else (lambda c, L, s, o: lp.lp_map_t
 for _ in range(5):
     mapf(ctx, L, specs, outs)
 lp.lp_sync_status(ctx)
+if {whole}:
+    # whole maps, CUDA events around each (the passes overlap as in use)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        mapf(ctx, L, specs, outs)
+        b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({{"map": sum(a.elapsed_time(b) for a, b in ev) / len(ev)}}))
+    lp.lp_destroy(ctx)
+    sys.exit(0)
 lp.lp_set_pass_timing(ctx, True)
 lp.lp_get_pass_timing(ctx)
 for _ in range(reps):
@@ -157,8 +169,12 @@ lp.lp_destroy(ctx)
 """
 
 
-def time_variant(lib: str, n: int, reps: int, side: int = 0, psf: int = 0, nspec: int = 1) -> Dict[str, float]:
-    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps, side=side, psf=psf, nspec=nspec)
+def time_variant(lib: str, n: int, reps: int, side: int = 0, psf: int = 0, nspec: int = 1,
+                 whole: bool = False) -> Dict[str, float]:
+    """Mean ms per launch of each pass (pass events), or with whole the mean
+    ms of whole maps ({"map": ms}), whose passes overlap as in use."""
+    code = _RUNNER.format(root=B.ROOT, lib=lib, n=n, reps=reps, side=side, psf=psf, nspec=nspec,
+                          whole="True" if whole else "False")
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     if res.returncode != 0:
         raise RuntimeError(f"timing failed for {lib}:\n{res.stderr[-2000:]}")
@@ -295,6 +311,33 @@ def tune_size(n: int, quick: bool, jobs: int, common: List[str], log, side: int 
         except Exception as e:
             log(f"  skip packed={int(p['packed'])}: {str(e).splitlines()[-1][:120]}")
     log(f"N={n}: packed={out.get('packed', False)}")
+    # whole-map refinement: the pass timings above stop the launch overlap
+    # between passes, which decides the trigger point and interacts with the
+    # forward row pass's resident blocks; time whole maps of the choice and
+    # of those neighbours, keep the fastest
+    reps = 200 if n <= 5200 else 40
+    late0 = list(out.get("late", B.DEFAULT_LATE))
+    cands = [dict(out, late=late0), dict(out, late=[0, 0, 0])]
+    m1 = out["minb"][0]
+    for mb in (m1 - 1, m1 + 1):
+        if 1 <= mb <= 3:
+            cands.append(dict(out, late=late0, minb=[mb] + list(out["minb"][1:])))
+    best_map = None
+    for p in cands:
+        lib = build_or_error(p)
+        if not isinstance(lib, str):
+            continue
+        try:
+            ms = min(time_variant(lib, n, reps, side, psf, nspec, whole=True)["map"] for _ in range(2))
+        except Exception as e:
+            log(f"  skip whole map late={p['late']} minb={p['minb']}: {str(e).splitlines()[-1][:120]}")
+            continue
+        log(f"  whole map late={p['late']} minb={p['minb']}: {ms * 1e3:.1f} us")
+        if best_map is None or ms < best_map[0] * 0.995:
+            best_map = (ms, p)
+    if best_map is not None:
+        out.update(late=best_map[1]["late"], minb=best_map[1]["minb"], tuned_map_us=best_map[0] * 1e3)
+    log(f"N={n}: late={out.get('late')} minb={out['minb']} (whole map {out.get('tuned_map_us', 0):.1f} us)")
     if nspec > 1:
         # several spectra: the batched column kernel against one single-
         # spectrum pass per spectrum
