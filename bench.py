@@ -77,7 +77,7 @@ def parse_args():
                          "tiled (17800 x 21000, 801^2 PSF, overlap-save tiles), "
                          "graph (loops of small maps as one CUDA-graph replay), "
                          "serve (Poisson requests at 130%% and at 70%% load)")
-    ap.add_argument("--forms-serve-requests", type=int, default=400)
+    ap.add_argument("--forms-serve-requests", type=int, default=2000)
     return ap.parse_args()
 
 
